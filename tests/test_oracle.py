@@ -1,0 +1,288 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix
+(no GPU needed).  Each test names the passage it checks.
+
+* printed FCI energy (Sec. Results, N=2 / M=7) -> ED Hamiltonian + Madelung
+* non-interacting limit: Fermi-Dirac G, closed-form grand potential
+* HS sum of squares reproduces V_ee (Sec. UEG, A(Q), B(Q)) in Fock space
+* Wick / Eq. green: the local energy and ln det from G equal exact Fock-space
+  traces of a one-body Gaussian operator
+* stabilisation invariance, equivalence of the stable-G forms
+* the optimal force bias cancels the O(sqrt(dtau)) term (Eq. import)
+* unconstrained (free-projection) AFQMC reproduces exact diagonalisation
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import afqmc, ed
+from oracle.ueg import UEG, fermi_dirac, basis_integer_vectors
+from synthetic_inputs import gaussian_fields
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def cfg1(**kw):
+    return UEG(2, 7, 1.0, 0.5, 0.05, **kw)
+
+
+# ------------------------------------------------------------------ setup
+@pytest.mark.parametrize("M,ncut2", [(7, 1), (57, 5), (123, 9), (171, 11), (257, 16)])
+def test_basis_and_transfer_counts(M, ncut2):
+    """Plane-wave basis and momentum transfers, recounted by brute force."""
+    nv = basis_integer_vectors(M)
+    assert len(nv) == M
+    assert max(int(n @ n) for n in nv) == ncut2
+    r = int(math.isqrt(ncut2))
+    brute = {n for n in itertools.product(range(-r, r + 1), repeat=3) if sum(c * c for c in n) <= ncut2}
+    assert {tuple(int(c) for c in n) for n in nv} == brute
+    diffs = {tuple(a - b for a, b in zip(p, q)) for p in brute for q in brute} - {(0, 0, 0)}
+    if M <= 123:
+        s = UEG(14 if M > 7 else 2, M, 1.0, 0.5, 0.05)
+        assert s.NQ == len(diffs) == s.N_alpha
+        half = {tuple(int(c) for c in q) for q in s.q_half}
+        assert all(tuple(-c for c in q) not in half for q in half)
+        # every off-diagonal pair belongs to exactly one transfer list
+        npairs = sum(len(p) for p in s.pairs_plus) + sum(len(p) for p in s.pairs_minus)
+        assert npairs == M * (M - 1)
+    if M == 7:
+        assert len(diffs) == 24          # +-e_i (6), +-e_i+-e_j (12), +-2e_i (6)
+
+
+def test_box_and_temperature_config1():
+    """L = (4 pi N/3)^(1/3) r_s and k_B T_F = 1/2 (9 pi/4)^(2/3)/r_s^2."""
+    s = cfg1()
+    assert abs(s.L - (4 * math.pi * 2 / 3) ** (1 / 3)) < 1e-14
+    assert abs(s.beta - 1.0 / (0.5 * 0.5 * (9 * math.pi / 4) ** (2 / 3))) < 1e-14
+    assert s.n_slices == 22 and abs(s.dtau * 22 - s.beta) < 1e-14
+    f = fermi_dirac(s.eps, s.mu_T, s.beta)
+    assert abs(2 * f.sum() - 2.0) < 1e-12
+
+
+# ------------------------------------------------------------------ ED pins
+def test_printed_fci_energy():
+    """Sec. Results: FCI -0.23968 E_h/e for N=2, M=7, r_s=3, T=0."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "fci_n2_m7_rs3.txt")) if not l.startswith("#")]
+    N, M, rs, e_ref, tol = rows[0]
+    s = UEG(int(N), int(M), float(rs), 0.5, 0.05)
+    e = ed.ground_state_energy(s, 1, 1, (0, 0, 0)) / int(N)
+    assert abs(e - float(e_ref)) < float(tol)
+
+
+def test_ed_noninteracting_matches_closed_form():
+    """v(Q) = 0: <N> = 2 sum f_FD, <E> - E_M = 2 sum eps f_FD (Eq. Z)."""
+    s = cfg1()
+    E, Nn = ed.grand_canonical(s, interacting=False)
+    f = fermi_dirac(s.eps, s.mu, s.beta)
+    assert abs(Nn - 2 * f.sum()) < 1e-12
+    assert abs(E - s.E_M - 2 * (s.eps * f).sum()) < 1e-12
+
+
+def test_hs_sum_of_squares_reproduces_vee():
+    """-1/2 sum_alpha v_alpha^2 + sum_K delta_eps_K n_K == V_ee in Fock space
+    (Sec. UEG: V_ee = 1/4 sum_Q [A^2 + B^2]; readings B and C)."""
+    s = cfg1()
+    H, *_ = ed.hamiltonian(s)
+    H0, *_ = ed.hamiltonian(s, interacting=False)
+    vee = H - H0
+    acc = sp.csr_matrix(H.shape, dtype=np.complex128)
+    for a in range(s.N_alpha):
+        y = np.zeros(s.N_alpha)
+        y[a] = 1.0
+        op = ed.one_body_operator(s.M, afqmc.hs_matrix(s, y) / math.sqrt(s.dtau))
+        acc = acc + op @ op
+    h1 = ed.one_body_operator(s.M, np.diag(s.delta_eps).astype(np.complex128))
+    assert abs(vee - (-0.5 * acc + h1)).max() < 1e-12
+    assert abs(vee).max() > 1.0
+
+
+def _wick_vs_trace(s, X):
+    H, *_ = ed.hamiltonian(s)
+    Nd, _, _ = ed.number_operator_diagonal(s.M)
+    Nop = sp.diags(Nd.astype(np.float64)).tocsr()
+    (avgH, avgN), lnZ = ed.gaussian_state_average(s.M, X, [H, Nop])
+    A = sla.expm(X)
+    G = np.linalg.inv(np.eye(s.M) + A)
+    E, Nloc = afqmc.local_energy(s, G)
+    sign, la = np.linalg.slogdet(np.eye(s.M) + A)
+    return avgH + s.E_M, avgN, lnZ, E, Nloc, 2 * (la + 1j * np.angle(sign))
+
+
+def test_local_energy_matches_fock_trace():
+    """Eq. green + Wick: for U = exp(sum X_ij a+_i a_j) (both spins),
+    tr(U H)/tr U = E_M + E_1 + E_2 from P = I - G^T, G = (I + e^X)^-1,
+    tr(U N)/tr U = 2 tr P and ln tr U = 2 ln det(I + e^X)."""
+    s = cfg1()
+    rng = np.random.default_rng(3)
+    X = 0.4 * (rng.standard_normal((7, 7)) + 1j * rng.standard_normal((7, 7))) - np.diag(s.eps - 1.0)
+    eH, eN, lnZ, E, Nloc, ld2 = _wick_vs_trace(s, X)
+    assert abs(E - eH) < 1e-10 * max(1, abs(eH))
+    assert abs(Nloc - eN) < 1e-10
+    d = ld2 - lnZ
+    assert abs(d.real) < 1e-10 and abs(math.remainder(d.imag, 2 * math.pi)) < 1e-10
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Planted in the oracle: a dropped exchange factor breaks the Fock-trace
+    pin; a transposed P (I - G instead of I - G^T) leaves the energy alone
+    (E is invariant under P -> P^T for the UEG) but breaks the force-bias pin."""
+    s = cfg1()
+    rng = np.random.default_rng(3)
+    X = 0.4 * (rng.standard_normal((7, 7)) + 1j * rng.standard_normal((7, 7))) - np.diag(s.eps - 1.0)
+    good = afqmc.local_energy(s, np.linalg.inv(np.eye(7) + sla.expm(X)))[0]
+    with monkeypatch.context() as m:
+        m.setattr(afqmc, "_shifted_pairs", lambda sys, sgn, q: (np.zeros(0, int), np.zeros(0, int)))
+        eH, _, _, E, _, _ = _wick_vs_trace(s, X)
+        assert abs(E - eH) > 1e-3 and abs(good - eH) < 1e-10
+    with monkeypatch.context() as m:
+        m.setattr(afqmc, "one_rdm", lambda G: np.eye(G.shape[0]) - G)
+        nb, g_ok, _ = _force_bias_gradients(5, 6)
+        assert g_ok > 0.5 * nb
+
+
+# ------------------------------------------------------------------ one-body pieces
+def test_hs_matrix_antihermitian_and_unitary():
+    """Reading B: for real y, V = sqrt(dtau) y.v is anti-Hermitian, exp(V) unitary."""
+    s = UEG(14, 57, 1.0, 0.125, 0.05)
+    y = np.random.default_rng(0).standard_normal(s.N_alpha)
+    V = afqmc.hs_matrix(s, y)
+    assert np.abs(V + V.conj().T).max() < 1e-15
+    assert np.all(np.diag(V) == 0)
+    E = sla.expm(V)
+    assert np.abs(E.conj().T @ E - np.eye(s.M)).max() < 1e-12
+    # Taylor(6) truncation error against Pade, reported as a number
+    err = np.abs(afqmc.expm_taylor(V, 6) - E).max()
+    assert err < 1e-5
+    assert np.abs(afqmc.expm_taylor(V, 20) - E).max() < 1e-13
+
+
+def test_noninteracting_path_closed_forms():
+    """v(Q) = 0, mu != mu_T: G(beta) = diag(1 - f_FD), 2 ln det(I + A) = ln Z_0,
+    and every intermediate ln det(I + B_T^(n-k) B^k) in closed form
+    (Eqs. grand2, green, Abrenda), through the stabilised chain."""
+    for (N, M, rs, th, dt) in [(2, 7, 1.0, 0.5, 0.05), (14, 57, 1.0, 0.125, 0.05)]:
+        s = UEG(N, M, rs, th, dt, interacting=False)
+        s.mu = s.mu_T + 0.3
+        f = gaussian_fields(5, s.n_slices, 1, s.N_alpha)[:, 0]
+        r = afqmc.propagate_walker(s, f, afqmc.Options(green="paper"), record=True)
+        fd = fermi_dirac(s.eps, s.mu, s.beta)
+        assert np.abs(r.G - np.diag(1 - fd)).max() < 1e-12
+        for k, ld in enumerate(r.logdet_trace, start=1):
+            a = -(s.n_slices - k) * s.dtau * (s.eps - s.mu_T) - k * s.dtau * (s.eps - s.mu)
+            ref = np.sum(np.log1p(np.exp(a)))
+            assert abs(ld.real - ref) < 1e-12 * abs(ref) + 1e-12
+        assert abs(r.number - 2 * fd.sum()) < 1e-11
+        assert abs(r.energy - s.E_M - 2 * (s.eps * fd).sum()) < 1e-10
+
+
+def test_green_forms_agree():
+    """Reading F: the paper's QDT form, the two-sided form and the direct
+    inverse give the same G(tau) and ln det on every slice."""
+    s = cfg1()
+    f = gaussian_fields(11, s.n_slices, 2, s.N_alpha)
+    R = {g: afqmc.run(s, f, afqmc.Options(green=g), record=True) for g in ("paper", "two_sided", "direct")}
+    for w in range(2):
+        for g in ("two_sided", "direct"):
+            assert np.abs(R[g][w].G - R["paper"][w].G).max() < 1e-12
+            for a, b in zip(R[g][w].logdet_trace, R["paper"][w].logdet_trace):
+                assert abs(a.real - b.real) < 1e-12
+                assert abs(math.remainder(a.imag - b.imag, 2 * math.pi)) < 1e-12
+    s = UEG(14, 57, 1.0, 0.125, 0.05)
+    f = gaussian_fields(12, s.n_slices, 1, s.N_alpha)
+    a = afqmc.run(s, f, afqmc.Options(green="paper"))[0]
+    b = afqmc.run(s, f, afqmc.Options(green="two_sided"))[0]
+    assert np.abs(a.G - b.G).max() < 1e-11
+    assert abs(a.logw - b.logw) < 1e-10 * max(1, abs(a.logw))
+
+
+def test_stabilisation_invariance():
+    """Sec. Numerical Stabilization: G and ln det do not depend on how often
+    the QRCP is applied (short chains)."""
+    for s, n in ((cfg1(), None), (UEG(14, 57, 1.0, 0.125, 0.05), 10)):
+        f = gaussian_fields(13, s.n_slices, 1, s.N_alpha)
+        res = [afqmc.run(s, f, afqmc.Options(stabilise_every=e, green="two_sided"), n_slices=n)[0]
+               for e in (0, 1, 5)]
+        for r in res[1:]:
+            assert np.abs(r.G - res[0].G).max() < 1e-12
+            assert abs(r.logdet.real - res[0].logdet.real) < 1e-12 * abs(res[0].logdet.real)
+            assert abs(r.logw - res[0].logw) < 1e-11
+
+
+def test_free_projection_weight_equals_product_determinant():
+    """Telescoping of Eq. ftoratio: the free-projection log weight equals
+    2 ln det(I + prod_k B(x_k - xbar_k)) - 2 ln det(I + B_T^n) plus the
+    Gaussian factors of Eq. import, with the product formed explicitly."""
+    s = cfg1()
+    o = afqmc.Options(constraint="free", green="two_sided")
+    f = gaussian_fields(14, s.n_slices, 1, s.N_alpha)[:, 0]
+    r = afqmc.propagate_walker(s, f, o, record=True, want_estimator=False)
+    A = np.eye(s.M, dtype=np.complex128)
+    gauss = 0j
+    for k in range(s.n_slices):
+        xb = r.xbar_trace[k]
+        A = afqmc.propagator(s, f[k] - xb, o.exp_order) @ A
+        gauss += np.sum(f[k] * xb - 0.5 * xb * xb)
+    sign, la = np.linalg.slogdet(np.eye(s.M) + A)
+    ref = 2 * (la + 1j * np.angle(sign)) - 2 * np.sum(np.log1p(afqmc.left_diagonal(s, 0))) + gauss
+    assert abs(r.logw.real - ref.real) < 1e-11
+    assert abs(math.remainder(r.logw.imag - ref.imag, 2 * math.pi)) < 1e-11
+
+
+def _force_bias_gradients(seed, kk):
+    s = cfg1()
+    f = gaussian_fields(seed, s.n_slices, 1, s.N_alpha)[:, 0]
+    o = afqmc.Options(green="two_sided")
+    st = afqmc.initial_state(s)
+    for k in range(1, kk):
+        st, *_ = afqmc.slice_step(s, st, f[k - 1], k, o)
+    xbar = afqmc.force_bias(s, st.G)
+
+    def grad(sign):
+        def lnI(x):
+            _, lnS, _, _ = afqmc.slice_step(s, st, sign * x, kk, o, xbar=sign * xbar)
+            return lnS + np.sum(x * xbar - 0.5 * xbar * xbar)
+        h = 1e-5
+        return np.array([(lnI(h * e) - lnI(-h * e)) / (2 * h) for e in np.eye(s.N_alpha)])
+    return np.linalg.norm(xbar), np.linalg.norm(grad(+1)), np.linalg.norm(grad(-1))
+
+
+@pytest.mark.parametrize("seed,kk", [(5, 6), (6, 12)])
+def test_force_bias_cancels_linear_term(seed, kk):
+    """Readings A and P: with exp(+sqrt(dtau)(x - xbar).v) and P(tau) the
+    equal-time 1RDM, d ln I_k / dx at x = 0 is O(dtau), far below |xbar| =
+    O(sqrt(dtau)); the opposite HS sign leaves about 2 |xbar|."""
+    nb, g_ok, g_wrong = _force_bias_gradients(seed, kk)
+    assert nb > 1e-2
+    assert g_ok < 0.3 * nb
+    assert g_wrong > 1.0 * nb
+
+
+# ------------------------------------------------------------------ end to end vs ED
+def _jackknife_ratio(w, E, nb=20):
+    W = len(w)
+    idx = np.array_split(np.arange(W), nb)
+    full = (np.sum(w * E) / np.sum(w)).real
+    jk = np.array([(np.sum(np.delete(w, b) * np.delete(E, b)) / np.sum(np.delete(w, b))).real for b in idx])
+    return full, math.sqrt((nb - 1) / nb * np.sum((jk - jk.mean()) ** 2))
+
+
+@pytest.mark.slow
+def test_free_projection_matches_exact_diagonalisation():
+    """Unconstrained AFQMC (Eqs. grand2 and import with complex weights) is
+    exact up to the Trotter error: config N=2, M=7, r_s=1, Theta=0.5."""
+    s = cfg1()
+    E_ed, N_ed = ed.grand_canonical(s)
+    W = 1500
+    f = gaussian_fields(7, s.n_slices, W, s.N_alpha)
+    res = afqmc.run(s, f, afqmc.Options(constraint="free", green="two_sided"))
+    lw = np.array([r.logw for r in res])
+    w = np.exp(lw - lw.real.max())
+    E, eE = _jackknife_ratio(w, np.array([r.energy for r in res]))
+    Nn, eN = _jackknife_ratio(w, np.array([r.number for r in res]))
+    assert abs(E - E_ed) < 3 * eE + 5e-3, (E, eE, E_ed)
+    assert abs(Nn - N_ed) < 3 * eN + 2e-3, (Nn, eN, N_ed)
+    assert eE < 0.02 and eN < 0.002
