@@ -1,0 +1,159 @@
+/*
+ * ftq.h -- C ABI of the GB300 walker-propagation library for phaseless
+ * finite-temperature AFQMC (ph-FT-AFQMC) of the 3D uniform electron gas in a
+ * plane-wave basis (Lee, Morales, Malone, arXiv:2012.12228).
+ *
+ * The library owns all walker state in device memory and runs every step of
+ * the path in its own sm_103a kernels; there is no CPU fallback.  Calls are
+ * ordered on the CUDA stream given in ftq_opts (NULL: the legacy default
+ * stream).  Caller buffers are read or written during the call's stream
+ * order and never retained.
+ *
+ * Every function returns FTQ_OK (0) or a negative status; the message of the
+ * last failure is available from ftq_last_error().
+ *
+ * Conventions (fixed, independent of precision):
+ *   basis     integer vectors n with |n|^2 <= ncut2 (closed shell with M
+ *             members), K = 2 pi n / L, ordered by (|n|^2, nx, ny, nz).
+ *   transfers every nonzero n_K' - n_K; the half space is the set whose first
+ *             nonzero component is positive, ordered by (|n|^2, nx, ny, nz).
+ *             Field alpha = 2q is the A(Q_q) field, alpha = 2q + 1 the B(Q_q)
+ *             field, N_alpha = number of all nonzero transfers.
+ *   G         complex128 [W][M][M] row-major, G_ij = <c_i c_j^+> for one spin
+ *             block (both spin blocks are identical for the unpolarised gas),
+ *             the equal-time Green's function at the current imaginary time.
+ */
+#ifndef FTQ_H
+#define FTQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FTQ_OK        0
+#define FTQ_EINVAL   -1   /* bad argument or call out of sequence            */
+#define FTQ_ECUDA    -2   /* a CUDA runtime call or kernel launch failed      */
+#define FTQ_ENUMERIC -3   /* singular pivot or non-finite log-determinant     */
+#define FTQ_ETIMEOUT -4   /* a bounded host wait expired                      */
+#define FTQ_ENOMEM   -5   /* device allocation failed                         */
+
+/* precision of the slice chain */
+#define FTQ_FP64   0      /* every step in complex128                                   */
+#define FTQ_MIXED  1      /* B chain in FP32-accurate tensor-core math, FP64 QR/UDT,
+                             FP64 determinants and weights                               */
+
+/* weight update */
+#define FTQ_PHASELESS 0   /* w <- |I_k| max(0, cos theta_k)  (Eqs. import, phimport, theta) */
+#define FTQ_FREE      1   /* w <- w I_k, complex (unconstrained free projection)            */
+
+typedef struct ftq_ctx ftq_ctx;
+
+typedef struct {
+    int      walkers;          /* W > 0                                                  */
+    int      stabilise_every;  /* s: QRCP of the right block every s slices (0 = never)   */
+    int      exp_order;        /* p >= 1: Taylor order of exp(V)                          */
+    int      precision;        /* FTQ_FP64 or FTQ_MIXED                                   */
+    int      constraint;       /* FTQ_PHASELESS or FTQ_FREE                               */
+    int      reserved;         /* must be 0                                               */
+    uint64_t seed;             /* reserved for the on-device field generator              */
+    void*    cuda_stream;      /* cudaStream_t the library launches on (NULL = default)  */
+    double   force_bias_cap;   /* 0 = off (no cap is applied in this version)             */
+} ftq_opts;
+
+/* Create a UEG system and W walkers at tau = 0 (A(0) = B_T^n).
+ *   N      target electron number N-bar (even, 0 < N < 2M)
+ *   M      plane-wave basis size; must be a closed-shell count (7, 19, 27, 33, 57, ...)
+ *   rs     Wigner-Seitz radius;  L = (4 pi N / 3)^(1/3) rs     (Computational Details)
+ *   theta  T / T_F with k_B T_F = (9 pi / 4)^(2/3) / (2 rs^2)  (Eq. fermiT)
+ *   mu     chemical potential of B; NaN selects mu = mu_T      (Sec. Phaseless approximation)
+ *   dtau   requested time step; n = round(beta / dtau) slices and dtau := beta / n
+ * The free-electron trial B_T = exp(-dtau (|K|^2/2 - mu_T)) uses mu_T tuned so
+ * that 2 sum_K f_FD = N (Sec. Results, FE trial; Computational Details).
+ * Allocates the device walker state (library-owned, freed by ftq_destroy).
+ * Errors: FTQ_EINVAL (bad parameters), FTQ_ENOMEM, FTQ_ECUDA. */
+int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu,
+                 double dtau, const ftq_opts* opts);
+
+/* Return every walker to tau = 0 (k = 0, unit weights, all alive). */
+int ftq_reset(ftq_ctx* ctx);
+
+/* Propagate all walkers over the next n_slices imaginary-time slices
+ * (Eqs. B, Abrenda, ftoratio, import, phimport; Sec. Numerical Stabilization).
+ * Per slice k: force bias from P(tau_{k-1}) (the optimal force bias), shifted
+ * fields y = x - xbar, B_k = e^{-dtau K/2} e^{V(y)} e^{-dtau K/2} applied to the
+ * right block, QRCP every s slices, G(tau_k) and ln det(I + A(tau_k)), and the
+ * weight update.
+ *   fields_dev  device pointer, float64 [n_slices][W][N_alpha] C order, N(0,1)
+ *               draws x_k, caller-owned; must not be NULL in this version.
+ * The slice counter may not pass n (FTQ_EINVAL).  Asynchronous: numeric
+ * breakdown is latched on the device and reported by ftq_status(). */
+int ftq_propagate_slices(ftq_ctx* ctx, int n_slices, const double* fields_dev);
+
+/* Force a QRCP refresh of the right block now (Sec. Numerical Stabilization).
+ * A(tau) and G(tau) are unchanged up to rounding. */
+int ftq_stabilise(ftq_ctx* ctx);
+
+/* Copy G(tau) of every walker into G_dev (device, complex128 [W][M][M],
+ * row-major, caller-owned).  Eq. green; at tau = beta this is (I + A)^-1. */
+int ftq_green(ftq_ctx* ctx, void* G_dev);
+
+/* Estimators at the current tau from P = I - G^T (Sec. UEG, local energy):
+ * N = 2 tr P, E = E_M + E_1 + E_2 with Gamma_Q and Lambda_Q, per walker, and
+ * the weighted sums over walkers (Theory: <O> = sum w O_L / sum w).
+ *   out_host        host, 8 doubles: {Re sum w, Im sum w, Re sum wE, Im sum wE,
+ *                   Re sum wN, Im sum wN, s, n_alive} where every w is scaled by
+ *                   exp(-s), s = max_i ln|w_i| over live walkers.
+ *   per_walker_dev  nullable device float64 [W][8]: {ln|w|, arg w, alive,
+ *                   Re E, Im E, Re N, Im N, unused}.
+ * Synchronises the stream. */
+int ftq_estimators(ftq_ctx* ctx, double* out_host, double* per_walker_dev);
+
+/* Per-walker weights and determinants: device float64 [W][8]
+ * {ln|w|, arg w, alive, Re ln det(I+A), Im ln det(I+A), Re gauss_k,
+ *  Im gauss_k, unused} where gauss_k = x_k.xbar_k - xbar_k.xbar_k / 2 of the
+ * last slice (Eq. import). */
+int ftq_weights(ftq_ctx* ctx, double* out_dev);
+
+/* Read and clear the latched device status (FTQ_OK or FTQ_ENUMERIC);
+ * synchronises the stream. */
+int ftq_status(ftq_ctx* ctx, int* status_host);
+
+/* Integer properties. */
+#define FTQ_Q_M          0
+#define FTQ_Q_N_ALPHA    1
+#define FTQ_Q_N_SLICES   2
+#define FTQ_Q_SLICE      3   /* slices propagated since the last reset */
+#define FTQ_Q_WALKERS    4
+#define FTQ_Q_NCUT2      5
+#define FTQ_Q_PRECISION  6
+#define FTQ_Q_DEVICE_BYTES 7 /* device bytes owned by the context */
+int ftq_query(const ftq_ctx* ctx, int key, int64_t* value);
+
+/* Floating-point properties. */
+#define FTQ_F_BETA   0
+#define FTQ_F_DTAU   1
+#define FTQ_F_MU     2
+#define FTQ_F_MU_T   3
+#define FTQ_F_L      4
+#define FTQ_F_E_M    5   /* E_M = N-bar * (-2.837297 / L) / 2 (Sec. UEG, Madelung term) */
+int ftq_query_f64(const ftq_ctx* ctx, int key, double* value);
+
+/* Host copies of the conventions: basis integer vectors [M][3] and
+ * half-space transfers [N_alpha/2][3] (int32, host buffers, caller-owned). */
+int ftq_basis(const ftq_ctx* ctx, int32_t* nvec_host);
+int ftq_transfers(const ftq_ctx* ctx, int32_t* q_host);
+
+/* Message of the last failure on ctx (or of the last failed ftq_init_ueg
+ * when ctx is NULL).  Never NULL. */
+const char* ftq_last_error(const ftq_ctx* ctx);
+
+/* Free the context and its device memory.  NULL is accepted. */
+void ftq_destroy(ftq_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTQ_H */

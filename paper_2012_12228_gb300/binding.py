@@ -1,0 +1,184 @@
+"""ctypes binding of the C ABI in include/ftq.h (argument marshalling only).
+
+Device buffers are torch tensors; the binding passes their data pointers and
+the current CUDA stream.  Every call checks the returned status and raises
+``FTQError`` with the library's message.
+"""
+import ctypes
+import math
+import os
+
+FTQ_FP64, FTQ_MIXED = 0, 1
+FTQ_PHASELESS, FTQ_FREE = 0, 1
+_Q = dict(M=0, N_ALPHA=1, N_SLICES=2, SLICE=3, WALKERS=4, NCUT2=5, PRECISION=6, DEVICE_BYTES=7)
+_F = dict(BETA=0, DTAU=1, MU=2, MU_T=3, L=4, E_M=5)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+class FTQError(RuntimeError):
+    pass
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("walkers", ctypes.c_int), ("stabilise_every", ctypes.c_int),
+                ("exp_order", ctypes.c_int), ("precision", ctypes.c_int),
+                ("constraint", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
+                ("force_bias_cap", ctypes.c_double)]
+
+
+EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
+           "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
+           "ftq_basis", "ftq_transfers", "ftq_last_error", "ftq_destroy"]
+
+
+def library_path():
+    return os.path.join(HERE, "_build", "libftq.so")
+
+
+def load_library(path=None):
+    """Load libftq.so (built by ``paper_2012_12228_gb300.build``); raises if absent."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise FTQError(f"{p} not found: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(p)
+    vp, i, d, i64p, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    lib.ftq_init_ueg.argtypes = [ctypes.POINTER(vp), i, i, d, d, d, d, ctypes.POINTER(Opts)]
+    lib.ftq_reset.argtypes = [vp]
+    lib.ftq_propagate_slices.argtypes = [vp, i, vp]
+    lib.ftq_stabilise.argtypes = [vp]
+    lib.ftq_green.argtypes = [vp, vp]
+    lib.ftq_estimators.argtypes = [vp, dp, vp]
+    lib.ftq_weights.argtypes = [vp, vp]
+    lib.ftq_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.ftq_query.argtypes = [vp, i, i64p]
+    lib.ftq_query_f64.argtypes = [vp, i, dp]
+    lib.ftq_basis.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.ftq_transfers.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.ftq_last_error.argtypes = [vp]
+    lib.ftq_last_error.restype = ctypes.c_char_p
+    lib.ftq_destroy.argtypes = [vp]
+    lib.ftq_destroy.restype = None
+    for name in EXPORTS[:-2]:
+        if name != "ftq_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+class Propagator:
+    """One UEG system with W walkers on the current CUDA device.
+
+    Parameters mirror ftq_init_ueg; ``mu=None`` selects mu = mu_T."""
+
+    def __init__(self, N, M, rs, theta, dtau, mu=None, walkers=64, stabilise_every=5,
+                 exp_order=6, precision=FTQ_FP64, constraint=FTQ_PHASELESS, seed=0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise FTQError("no CUDA device: the propagator has no CPU path")
+        self._torch = torch
+        self.lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o = Opts(walkers, stabilise_every, exp_order, precision, constraint, 0, seed,
+                 ctypes.c_void_p(self.stream.cuda_stream), 0.0)
+        h = ctypes.c_void_p()
+        st = self.lib.ftq_init_ueg(ctypes.byref(h), N, M, rs, theta,
+                                   float("nan") if mu is None else float(mu), dtau, ctypes.byref(o))
+        if st != 0:
+            raise FTQError(f"ftq_init_ueg: {self.lib.ftq_last_error(None).decode()} (status {st})")
+        self.h = h
+        self.W = walkers
+        self.M = self.query("M")
+        self.n_alpha = self.query("N_ALPHA")
+        self.n_slices = self.query("N_SLICES")
+
+    def _check(self, st, what):
+        if st != 0:
+            raise FTQError(f"{what}: {self.lib.ftq_last_error(self.h).decode()} (status {st})")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ftq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, key):
+        v = ctypes.c_int64()
+        self._check(self.lib.ftq_query(self.h, _Q[key], ctypes.byref(v)), "ftq_query")
+        return v.value
+
+    def query_f64(self, key):
+        v = ctypes.c_double()
+        self._check(self.lib.ftq_query_f64(self.h, _F[key], ctypes.byref(v)), "ftq_query_f64")
+        return v.value
+
+    def basis(self):
+        buf = (ctypes.c_int32 * (3 * self.M))()
+        self._check(self.lib.ftq_basis(self.h, buf), "ftq_basis")
+        return [tuple(buf[3 * i:3 * i + 3]) for i in range(self.M)]
+
+    def transfers(self):
+        n = self.n_alpha // 2
+        buf = (ctypes.c_int32 * (3 * n))()
+        self._check(self.lib.ftq_transfers(self.h, buf), "ftq_transfers")
+        return [tuple(buf[3 * i:3 * i + 3]) for i in range(n)]
+
+    def reset(self):
+        self._check(self.lib.ftq_reset(self.h), "ftq_reset")
+
+    def propagate(self, fields):
+        """fields: CUDA float64 tensor [n][W][N_alpha] (contiguous)."""
+        t = self._torch
+        if fields.device.type != "cuda" or fields.dtype != t.float64 or not fields.is_contiguous():
+            raise FTQError("fields must be a contiguous CUDA float64 tensor")
+        if fields.dim() != 3 or fields.shape[1] != self.W or fields.shape[2] != self.n_alpha:
+            raise FTQError(f"fields must have shape [n, {self.W}, {self.n_alpha}]")
+        self._check(self.lib.ftq_propagate_slices(self.h, int(fields.shape[0]), ctypes.c_void_p(fields.data_ptr())),
+                    "ftq_propagate_slices")
+
+    def stabilise(self):
+        self._check(self.lib.ftq_stabilise(self.h), "ftq_stabilise")
+
+    def green(self, out=None):
+        t = self._torch
+        if out is None:
+            out = t.empty((self.W, self.M, self.M), dtype=t.complex128, device="cuda")
+        self._check(self.lib.ftq_green(self.h, ctypes.c_void_p(out.data_ptr())), "ftq_green")
+        return out
+
+    def weights(self):
+        t = self._torch
+        out = t.empty((self.W, 8), dtype=t.float64, device="cuda")
+        self._check(self.lib.ftq_weights(self.h, ctypes.c_void_p(out.data_ptr())), "ftq_weights")
+        return out
+
+    def estimators(self, per_walker=True):
+        t = self._torch
+        pw = t.empty((self.W, 8), dtype=t.float64, device="cuda") if per_walker else None
+        buf = (ctypes.c_double * 8)()
+        self._check(self.lib.ftq_estimators(self.h, buf, ctypes.c_void_p(pw.data_ptr()) if pw is not None else None),
+                    "ftq_estimators")
+        sw = complex(buf[0], buf[1])
+        res = dict(sum_w=sw, sum_wE=complex(buf[2], buf[3]), sum_wN=complex(buf[4], buf[5]),
+                   log_scale=buf[6], n_alive=int(buf[7]))
+        res["E"] = res["sum_wE"] / sw if sw != 0 else complex(math.nan, math.nan)
+        res["N"] = res["sum_wN"] / sw if sw != 0 else complex(math.nan, math.nan)
+        if pw is not None:
+            res["per_walker"] = pw
+        return res
+
+    def status(self):
+        v = ctypes.c_int()
+        self._check(self.lib.ftq_status(self.h, ctypes.byref(v)), "ftq_status")
+        return v.value

@@ -1,0 +1,262 @@
+// C ABI of the walker-propagation library: context lifetime, device
+// allocations, and the per-slice launch sequence.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ftq_internal.h"
+
+namespace {
+
+thread_local std::string g_init_error;
+
+int fail(ftq_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg; else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(ftq_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, FTQ_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t dalloc(ftq_ctx* c, T** p, size_t n) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * n);
+    if (e == cudaSuccess) c->bytes += sizeof(T) * n;
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(ftq_ctx* c, T** p, const std::vector<T>& v) {
+    cudaError_t e = dalloc(c, p, v.size() ? v.size() : 1);
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_all(ftq_ctx* c) {
+    void* ptrs[] = {c->Y, c->Tinv, c->G, c->work, c->work2, c->zbuf[0], c->zbuf[1], c->DR, c->phi,
+                    c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
+                    c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
+                    c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu, double dtau,
+                 const ftq_opts* opts) {
+    if (!out || !opts) return fail(nullptr, FTQ_EINVAL, "out and opts must not be NULL");
+    *out = nullptr;
+    if (opts->walkers <= 0) return fail(nullptr, FTQ_EINVAL, "walkers must be positive");
+    if (opts->exp_order < 1 || opts->exp_order > 32) return fail(nullptr, FTQ_EINVAL, "exp_order must be in 1..32");
+    if (opts->stabilise_every < 0) return fail(nullptr, FTQ_EINVAL, "stabilise_every must be >= 0");
+    if (opts->precision != FTQ_FP64 && opts->precision != FTQ_MIXED)
+        return fail(nullptr, FTQ_EINVAL, "unknown precision");
+    if (opts->constraint != FTQ_PHASELESS && opts->constraint != FTQ_FREE)
+        return fail(nullptr, FTQ_EINVAL, "unknown constraint");
+    if (opts->reserved != 0) return fail(nullptr, FTQ_EINVAL, "reserved field must be 0");
+    if (N % 2 != 0) return fail(nullptr, FTQ_EINVAL, "N must be even (unpolarised gas)");
+    ftq_ctx* c = new (std::nothrow) ftq_ctx();
+    if (!c) return fail(nullptr, FTQ_ENOMEM, "host allocation failed");
+    std::string why = ftq::build_ueg(c->sys, N, M, rs, theta, mu, dtau);
+    if (!why.empty()) {
+        delete c;
+        return fail(nullptr, FTQ_EINVAL, why);
+    }
+    if (M > 1024) {
+        delete c;
+        return fail(nullptr, FTQ_EINVAL, "M > 1024 is not supported by the per-walker factorisation kernels");
+    }
+    if (opts->precision == FTQ_MIXED) {
+        delete c;
+        return fail(nullptr, FTQ_EINVAL, "FTQ_MIXED is not available in this build");
+    }
+    c->opts = *opts;
+    c->stream = reinterpret_cast<cudaStream_t>(opts->cuda_stream);
+    c->W = opts->walkers;
+    c->M = M;
+    c->nslot = 2 * c->sys.nq_half + 1;
+    const size_t W = c->W, MM = (size_t)M * M;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    chk(dalloc(c, &c->Y, W * MM));
+    chk(dalloc(c, &c->Tinv, W * MM));
+    chk(dalloc(c, &c->G, W * MM));
+    chk(dalloc(c, &c->work, W * MM));
+    chk(dalloc(c, &c->work2, W * MM));
+    chk(dalloc(c, &c->zbuf[0], W * MM));
+    chk(dalloc(c, &c->zbuf[1], W * MM));
+    chk(dalloc(c, &c->DR, W * M));
+    chk(dalloc(c, &c->phi, W * c->nslot));
+    chk(dalloc(c, &c->hh, W * M));
+    chk(dalloc(c, &c->htau, W * M));
+    chk(dalloc(c, &c->perm, W * M));
+    chk(dalloc(c, &c->wstate, W * 8));
+    chk(dalloc(c, &c->est, W * 8));
+    chk(dalloc(c, &c->red, 8));
+    chk(dalloc(c, &c->status, 1));
+    const ftq::UegSetup& s = c->sys;
+    std::vector<double> h(M), ksq(M), g0(M);
+    for (int i = 0; i < M; ++i) {
+        h[i] = std::exp(-0.5 * s.dtau * (s.eps[i] + s.deps[i] - s.mu));
+        ksq[i] = 2.0 * s.eps[i];
+        g0[i] = 1.0 / (1.0 + std::exp(-s.beta * (s.eps[i] - s.mu_T)));
+    }
+    if (e == cudaSuccess) {
+        chk(upload(c, &c->tab.vidx, s.vidx));
+        chk(upload(c, &c->tab.pair_ptr, s.pair_ptr));
+        chk(upload(c, &c->tab.pair_a, s.pair_a));
+        chk(upload(c, &c->tab.pair_b, s.pair_b));
+        chk(upload(c, &c->tab.eps, s.eps));
+        chk(upload(c, &c->tab.h, h));
+        chk(upload(c, &c->tab.cq, s.cq));
+        chk(upload(c, &c->tab.vq, s.vq));
+        chk(upload(c, &c->tab.ksq, ksq));
+        chk(upload(c, &c->tab.g0, g0));
+    }
+    if (e == cudaSuccess) chk(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    if (e == cudaSuccess) chk(ftq::launch_init_walkers(c));
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? FTQ_ENOMEM : FTQ_ECUDA;
+        std::string msg = std::string("device setup failed: ") + cudaGetErrorString(e);
+        free_all(c);
+        delete c;
+        return fail(nullptr, code, msg);
+    }
+    *out = c;
+    return FTQ_OK;
+}
+
+int ftq_reset(ftq_ctx* c) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    cudaError_t e = ftq::launch_init_walkers(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reset");
+    return FTQ_OK;
+}
+
+int ftq_propagate_slices(ftq_ctx* c, int n_slices, const double* fields_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (n_slices < 0) return fail(c, FTQ_EINVAL, "n_slices must be >= 0");
+    if (c->k + n_slices > c->sys.n_slices)
+        return fail(c, FTQ_EINVAL, "propagation would pass tau = beta; call ftq_reset first");
+    if (n_slices > 0 && !fields_dev) return fail(c, FTQ_EINVAL, "fields_dev must not be NULL");
+    const size_t per_slice = (size_t)c->W * c->sys.n_alpha;
+    for (int t = 0; t < n_slices; ++t) {
+        const int k = c->k + 1;
+        cudaError_t e = ftq::launch_force_bias(c, fields_dev + per_slice * t);
+        if (e == cudaSuccess) e = ftq::launch_chain(c);
+        if (e == cudaSuccess && c->opts.stabilise_every > 0 && k % c->opts.stabilise_every == 0)
+            e = ftq::launch_qrcp(c);
+        if (e == cudaSuccess) e = ftq::launch_green(c, k, true);
+        if (e != cudaSuccess) return cuda_fail(c, e, "propagate");
+        c->k = k;
+    }
+    return FTQ_OK;
+}
+
+int ftq_stabilise(ftq_ctx* c) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    cudaError_t e = ftq::launch_qrcp(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stabilise");
+    return FTQ_OK;
+}
+
+int ftq_green(ftq_ctx* c, void* G_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!G_dev) return fail(c, FTQ_EINVAL, "G_dev must not be NULL");
+    cudaError_t e = ftq::launch_copy_green(c, reinterpret_cast<double2*>(G_dev));
+    if (e != cudaSuccess) return cuda_fail(c, e, "green");
+    return FTQ_OK;
+}
+
+int ftq_estimators(ftq_ctx* c, double* out_host, double* per_walker_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
+    cudaError_t e = ftq::launch_estimators(c, per_walker_dev);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, c->red, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "estimators");
+    return FTQ_OK;
+}
+
+int ftq_weights(ftq_ctx* c, double* out_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!out_dev) return fail(c, FTQ_EINVAL, "out_dev must not be NULL");
+    cudaError_t e = cudaMemcpyAsync(out_dev, c->wstate, sizeof(double) * 8 * c->W, cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "weights");
+    return FTQ_OK;
+}
+
+int ftq_status(ftq_ctx* c, int* status_host) {
+    if (!c || !status_host) return fail(c, FTQ_EINVAL, "NULL argument");
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status");
+    *status_host = v ? FTQ_ENUMERIC : FTQ_OK;
+    return FTQ_OK;
+}
+
+int ftq_query(const ftq_ctx* c, int key, int64_t* value) {
+    if (!c || !value) return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "NULL argument");
+    switch (key) {
+        case FTQ_Q_M: *value = c->M; break;
+        case FTQ_Q_N_ALPHA: *value = c->sys.n_alpha; break;
+        case FTQ_Q_N_SLICES: *value = c->sys.n_slices; break;
+        case FTQ_Q_SLICE: *value = c->k; break;
+        case FTQ_Q_WALKERS: *value = c->W; break;
+        case FTQ_Q_NCUT2: *value = c->sys.ncut2; break;
+        case FTQ_Q_PRECISION: *value = c->opts.precision; break;
+        case FTQ_Q_DEVICE_BYTES: *value = (int64_t)c->bytes; break;
+        default: return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "unknown query key");
+    }
+    return FTQ_OK;
+}
+
+int ftq_query_f64(const ftq_ctx* c, int key, double* value) {
+    if (!c || !value) return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "NULL argument");
+    switch (key) {
+        case FTQ_F_BETA: *value = c->sys.beta; break;
+        case FTQ_F_DTAU: *value = c->sys.dtau; break;
+        case FTQ_F_MU: *value = c->sys.mu; break;
+        case FTQ_F_MU_T: *value = c->sys.mu_T; break;
+        case FTQ_F_L: *value = c->sys.L; break;
+        case FTQ_F_E_M: *value = c->sys.E_M; break;
+        default: return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "unknown query key");
+    }
+    return FTQ_OK;
+}
+
+int ftq_basis(const ftq_ctx* c, int32_t* nvec_host) {
+    if (!c || !nvec_host) return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "NULL argument");
+    for (size_t i = 0; i < c->sys.nvec.size(); ++i) nvec_host[i] = c->sys.nvec[i];
+    return FTQ_OK;
+}
+
+int ftq_transfers(const ftq_ctx* c, int32_t* q_host) {
+    if (!c || !q_host) return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "NULL argument");
+    for (size_t i = 0; i < c->sys.qhalf.size(); ++i) q_host[i] = c->sys.qhalf[i];
+    return FTQ_OK;
+}
+
+const char* ftq_last_error(const ftq_ctx* c) {
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+void ftq_destroy(ftq_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the host orchestrator and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ftq.h"
+
+namespace ftq {
+
+// Static description of one UEG system (Sec. "Uniform Electron Gas" and
+// "Computational Details").  Built on the host once per context.
+struct UegSetup {
+    int N = 0, M = 0, ncut2 = 0, R = 0;       // R = isqrt(ncut2)
+    int nq_half = 0, n_alpha = 0, n_slices = 0;
+    double rs = 0, theta = 0, L = 0, Omega = 0, TF = 0, beta = 0, dtau = 0;
+    double mu = 0, mu_T = 0, E_M = 0;
+    std::vector<int> nvec;        // [M][3]
+    std::vector<int> qhalf;       // [nq_half][3]
+    std::vector<double> eps;      // |K|^2 / 2
+    std::vector<double> deps;     // one-body correction of the sum-of-squares form
+    std::vector<double> cq;       // sqrt(2 pi / (Omega Q^2)), half space
+    std::vector<double> vq;       // 4 pi / (Omega Q^2), half space
+    // slot of the phi table addressed by (K', K): 0 for K' == K, 1 + 2q for
+    // K' - K = +Q_q, 2 + 2q for K' - K = -Q_q.
+    std::vector<uint16_t> vidx;   // [M][M]
+    // pairs (a, b) with n_a - n_b = Q for every slot, CSR by slot
+    std::vector<int> pair_ptr;    // [2 nq_half + 2]
+    std::vector<int> pair_a, pair_b;
+};
+
+// Returns an empty string on success, else the reason.
+std::string build_ueg(UegSetup& s, int N, int M, double rs, double theta, double mu, double dtau);
+
+// Device-side constant tables.
+struct DevTables {
+    uint16_t* vidx = nullptr;     // [M][M]
+    int* pair_ptr = nullptr;      // [nslot + 1]
+    int* pair_a = nullptr;
+    int* pair_b = nullptr;
+    double* eps = nullptr;        // [M]
+    double* h = nullptr;          // exp(-dtau/2 (eps + deps - mu)) [M]
+    double* cq = nullptr;         // [nq_half]
+    double* vq = nullptr;         // [nq_half]
+    double* ksq = nullptr;        // |K|^2 [M]
+    double* g0 = nullptr;         // diagonal of G(0) = (I + B_T^n)^-1 [M]
+};
+
+}  // namespace ftq
+
+struct ftq_ctx {
+    ftq::UegSetup sys;
+    ftq::DevTables tab;
+    ftq_opts opts{};
+    cudaStream_t stream = nullptr;
+    int W = 0, M = 0, k = 0;
+    int nslot = 0;                // 2 nq_half + 1
+    // walker state (complex128 unless noted)
+    double2* Y = nullptr;         // chain: B's since the last QRCP times Q_R   [W][M][M]
+    double2* Tinv = nullptr;      // T_R^-1                                   [W][M][M]
+    double2* G = nullptr;         // G(tau_k)                                 [W][M][M]
+    double2* work = nullptr;      // LU / QR workspace                        [W][M][M]
+    double2* work2 = nullptr;     // triangular-solve workspace (column-major)[W][M][M]
+    double2* zbuf[2] = {nullptr, nullptr};   // Horner buffers                [W][M][M]
+    double2* DR = nullptr;        // D_R                                       [W][M]
+    double2* phi = nullptr;       // V generator table per walker              [W][nslot]
+    double2* hh = nullptr;        // Householder u_0 per column                [W][M]
+    double* htau = nullptr;       // Householder tau                           [W][M]
+    int* perm = nullptr;          // pivot permutation scratch                 [W][M]
+    double* wstate = nullptr;     // [W][8]: ln|w|, arg w, alive, Re ld, Im ld, Re gauss, Im gauss, tparity
+    double* est = nullptr;        // [W][8] per-walker estimators
+    double* red = nullptr;        // [8] reduced sums
+    int* status = nullptr;        // latched numeric status
+    size_t bytes = 0;
+    std::string err;
+};
+
+namespace ftq {
+
+// Kernel launchers (fp64_kernels.cu).  All asynchronous on ctx->stream.
+cudaError_t launch_init_walkers(ftq_ctx* c);
+cudaError_t launch_force_bias(ftq_ctx* c, const double* x);
+cudaError_t launch_chain(ftq_ctx* c);
+cudaError_t launch_qrcp(ftq_ctx* c);
+cudaError_t launch_green(ftq_ctx* c, int k, bool update_weights);
+cudaError_t launch_estimators(ftq_ctx* c, double* per_walker);
+cudaError_t launch_copy_green(ftq_ctx* c, double2* out);
+
+}  // namespace ftq
