@@ -146,6 +146,27 @@ int ftq_query_f64(const ftq_ctx* ctx, int key, double* value);
 int ftq_basis(const ftq_ctx* ctx, int32_t* nvec_host);
 int ftq_transfers(const ftq_ctx* ctx, int32_t* q_host);
 
+/* Kernel classes for launch accounting and timing. */
+#define FTQ_K_FORCE_BIAS 0   /* force bias + shifted fields + V generator table   */
+#define FTQ_K_CHAIN      1   /* one Taylor-Horner step of exp(V) on the chain       */
+#define FTQ_K_QRCP       2   /* QRCP stabilisation of the right block              */
+#define FTQ_K_GREEN      3   /* G(tau), ln det(I + A) and the weight update         */
+#define FTQ_K_ESTIMATORS 4   /* per-walker estimators and the walker reduction      */
+#define FTQ_K_INIT       5   /* walker initialisation / reset                      */
+#define FTQ_K_COUNT      8
+
+/* Start (enable != 0) or stop per-launch timing.  While on, every kernel
+ * launch is bracketed by a CUDA event pair on the context's stream; enabling
+ * clears the accumulated times.  Timing adds event records between launches
+ * and is meant for measurement runs only. */
+int ftq_profile(ftq_ctx* ctx, int enable);
+
+/* Synchronise the stream and return, per kernel class, the summed event time
+ * in milliseconds of the launches timed since profiling was enabled, and the
+ * number of launches made since the context was created (timed or not).
+ * Both arrays are host buffers of FTQ_K_COUNT entries; either may be NULL. */
+int ftq_profile_read(ftq_ctx* ctx, double* ms_host, int64_t* launches_host);
+
 /* Message of the last failure on ctx (or of the last failed ftq_init_ueg
  * when ctx is NULL).  Never NULL. */
 const char* ftq_last_error(const ftq_ctx* ctx);

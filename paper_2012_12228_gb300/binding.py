@@ -31,7 +31,10 @@ class Opts(ctypes.Structure):
 
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
-           "ftq_basis", "ftq_transfers", "ftq_last_error", "ftq_destroy"]
+           "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_last_error",
+           "ftq_destroy"]
+KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5}
+K_COUNT = 8
 
 
 def library_path():
@@ -60,6 +63,8 @@ def load_library(path=None):
     lib.ftq_query_f64.argtypes = [vp, i, dp]
     lib.ftq_basis.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.ftq_transfers.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.ftq_profile.argtypes = [vp, i]
+    lib.ftq_profile_read.argtypes = [vp, dp, i64p]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]
@@ -177,6 +182,19 @@ class Propagator:
         if pw is not None:
             res["per_walker"] = pw
         return res
+
+    def profile(self, enable=True):
+        self._check(self.lib.ftq_profile(self.h, 1 if enable else 0), "ftq_profile")
+
+    def profile_read(self):
+        """{kernel: (summed event ms of timed launches, launches so far)}"""
+        ms = (ctypes.c_double * K_COUNT)()
+        n = (ctypes.c_int64 * K_COUNT)()
+        self._check(self.lib.ftq_profile_read(self.h, ms, n), "ftq_profile_read")
+        return {k: (ms[v], n[v]) for k, v in KERNELS.items()}
+
+    def launches(self):
+        return sum(v[1] for v in self.profile_read().values())
 
     def status(self):
         v = ctypes.c_int()

@@ -247,6 +247,38 @@ int ftq_transfers(const ftq_ctx* c, int32_t* q_host) {
     return FTQ_OK;
 }
 
+int ftq_profile(ftq_ctx* c, int enable) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (enable) {
+        for (auto& sp : c->spans) { c->event_pool.push_back(sp.a); c->event_pool.push_back(sp.b); }
+        c->spans.clear();
+        for (int k = 0; k < FTQ_K_COUNT; ++k) { c->prof_ms[k] = 0; c->prof_n[k] = 0; }
+    }
+    c->prof = enable != 0;
+    return FTQ_OK;
+}
+
+int ftq_profile_read(ftq_ctx* c, double* ms_host, int64_t* launches_host) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    cudaError_t e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile_read");
+    for (auto& sp : c->spans) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, sp.a, sp.b);
+        if (e != cudaSuccess) return cuda_fail(c, e, "profile_read elapsed");
+        c->prof_ms[sp.kind] += ms;
+        c->prof_n[sp.kind] += 1;
+        c->event_pool.push_back(sp.a);
+        c->event_pool.push_back(sp.b);
+    }
+    c->spans.clear();
+    for (int k = 0; k < FTQ_K_COUNT; ++k) {
+        if (ms_host) ms_host[k] = c->prof_ms[k];
+        if (launches_host) launches_host[k] = c->launches[k];
+    }
+    return FTQ_OK;
+}
+
 const char* ftq_last_error(const ftq_ctx* c) {
     if (!c) return g_init_error.c_str();
     return c->err.c_str();
@@ -255,6 +287,8 @@ const char* ftq_last_error(const ftq_ctx* c) {
 void ftq_destroy(ftq_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    for (auto& sp : c->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+    for (auto ev : c->event_pool) cudaEventDestroy(ev);
     free_all(c);
     delete c;
 }

@@ -551,13 +551,16 @@ cudaError_t launch_init_walkers(ftq_ctx* c) {
     double ld0 = 0.0;
     for (int i = 0; i < M; ++i) ld0 += std::log1p(std::exp(-c->sys.beta * (c->sys.eps[i] - c->sys.mu_T)));
     long total = (long)W * M * M;
+    LaunchScope ls0(c, FTQ_K_INIT);
     k_init_matrices<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(c->Y, c->Tinv, c->G, c->tab.g0, M, total);
+    c->launches[FTQ_K_INIT] += 1;
     k_init_walkers<<<W, 64, 0, c->stream>>>(c->DR, c->wstate, M, W, ld0);
     c->k = 0;
     return cudaGetLastError();
 }
 
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x) {
+    LaunchScope ls(c, FTQ_K_FORCE_BIAS);
     k_force_bias<<<c->W, 256, 0, c->stream>>>(c->G, x, c->phi, c->wstate, c->tab.pair_ptr, c->tab.pair_a,
                                               c->tab.pair_b, c->tab.cq, c->M, c->sys.nq_half,
                                               std::sqrt(c->sys.dtau));
@@ -573,6 +576,7 @@ cudaError_t launch_chain(ftq_ctx* c) {
     int cur = 0;
     for (int j = p; j >= 1; --j) {
         double2* out = c->zbuf[cur];
+        LaunchScope ls(c, FTQ_K_CHAIN);
         k_chain_step<<<grid, 256, 0, c->stream>>>(zin, c->Y, out, c->phi, c->tab.vidx,
                                                   j == p ? c->tab.h : nullptr, c->tab.h,
                                                   j == 1 ? c->tab.h : nullptr, 1.0 / j, M, c->nslot, tiles);
@@ -590,8 +594,11 @@ cudaError_t launch_qrcp(ftq_ctx* c) {
     const int M = c->M;
     size_t sm = sizeof(double) * M + sizeof(int) * M;
     int nt = fact_threads(M);
+    {
+    LaunchScope ls(c, FTQ_K_QRCP);
     k_qrcp<<<c->W, nt, sm, c->stream>>>(c->Y, c->zbuf[0], c->work, c->work2, c->DR, c->Tinv, c->hh, c->htau,
                                        c->wstate, c->status, M);
+    }
     double2* q = c->zbuf[0];
     c->zbuf[0] = c->Y;
     c->Y = q;
@@ -604,6 +611,7 @@ cudaError_t launch_green(ftq_ctx* c, int k, bool update) {
     int nt = fact_threads(M);
     double lscale = (double)(c->sys.n_slices - k) * c->sys.dtau;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    LaunchScope ls(c, FTQ_K_GREEN);
     k_green<<<c->W, nt, sm, c->stream>>>(c->Y, c->Tinv, c->DR, c->work, c->work2, c->G, c->tab.eps, c->wstate,
                                         c->status, M, lscale, c->sys.mu_T, c->opts.constraint, update ? 1 : 0);
     return cudaGetLastError();
@@ -613,9 +621,11 @@ cudaError_t launch_estimators(ftq_ctx* c, double* per_walker) {
     const int M = c->M, nqh = c->sys.nq_half;
     size_t sm = sizeof(double2) * (2 * nqh + 1);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_estimators, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    LaunchScope ls(c, FTQ_K_ESTIMATORS);
     k_estimators<<<c->W, 256, sm, c->stream>>>(c->G, c->wstate, c->est, c->tab.pair_ptr, c->tab.pair_a,
                                                c->tab.pair_b, c->tab.vidx, c->tab.vq, c->tab.ksq, M, nqh,
                                                c->sys.E_M);
+    c->launches[FTQ_K_ESTIMATORS] += 1;
     k_reduce_walkers<<<1, 256, 0, c->stream>>>(c->est, c->red, c->W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

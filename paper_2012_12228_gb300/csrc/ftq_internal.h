@@ -75,9 +75,50 @@ struct ftq_ctx {
     int* status = nullptr;        // latched numeric status
     size_t bytes = 0;
     std::string err;
+    // launch accounting and optional per-launch CUDA-event timing
+    int64_t launches[FTQ_K_COUNT] = {};
+    bool prof = false;
+    struct Span { cudaEvent_t a, b; int kind; };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[FTQ_K_COUNT] = {};
+    int64_t prof_n[FTQ_K_COUNT] = {};
 };
 
 namespace ftq {
+
+inline cudaEvent_t pool_event(ftq_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one kernel launch: counts it, and when profiling is on records a
+// CUDA event pair on the context's stream around it.
+struct LaunchScope {
+    ftq_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    LaunchScope(ftq_ctx* c_, int k) : c(c_), kind(k) {
+        c->launches[k] += 1;
+        if (c->prof) {
+            a = pool_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~LaunchScope() {
+        if (c->prof && a) {
+            cudaEvent_t b = pool_event(c);
+            cudaEventRecord(b, c->stream);
+            c->spans.push_back({a, b, kind});
+        }
+    }
+};
 
 // Kernel launchers (fp64_kernels.cu).  All asynchronous on ctx->stream.
 cudaError_t launch_init_walkers(ftq_ctx* c);
