@@ -16,6 +16,7 @@ Multi-GPU (torchrun): independent replicas with different seeds, no
 collective on the data path; value = walker-slices of all ranks / max time.
 """
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -43,7 +44,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the complex128 comparison")
+    ap.add_argument("--no-compare", action="store_true", help="skip the complex128 comparison run")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed-vs-FP64 energy check")
     ap.add_argument("--walkers", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", nargs=2, type=int, default=None, metavar=("WALKERS", "SLICES"),
@@ -141,33 +145,158 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline
-def kernel_flops(kind, M, W, p, precision):
-    """Algorithmic real flops of ONE launch of a kernel class (complex MAC = 8)."""
+PEAKS = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+# FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def kernel_model(kind, M, W, precision):
+    """(algorithmic real flops of ONE launch, bound, peak TFLOP/s, peak source).
+
+    A complex multiply-add counts 8 real flops."""
+    fp64 = ("alu", FP64_PEAK_TFLOPS, "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz")
+    fp32 = ("alu", FP32_PEAK_TFLOPS, "FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz")
     if kind == "chain":          # one Horner step: V (M x M) times Z (M x M), per walker
-        return 8.0 * M ** 3 * W
+        return (8.0 * M ** 3 * W,) + (fp64 if precision == "fp64" else fp32)
     if kind == "green":          # LU (8/3 M^3) + two triangular solves with M right-hand sides (8 M^3)
-        return (8.0 / 3.0 + 8.0) * M ** 3 * W
+        return ((8.0 / 3.0 + 8.0) * M ** 3 * W,) + (fp64 if precision == "fp64" else fp32)
     if kind == "qrcp":           # Householder QR (16/3) + forming Q (16/3) + T^-1 update (4)
-        return (16.0 / 3.0 + 16.0 / 3.0 + 4.0) * M ** 3 * W
+        return ((16.0 / 3.0 + 16.0 / 3.0 + 4.0) * M ** 3 * W,) + fp64
     return None
 
 
-def roofline(prof, M, W, p, precision):
-    dom = max((k for k in prof if prof[k]["n_timed"] > 0), key=lambda k: prof[k]["ms"])
+def roofline(prof, M, W, precision):
+    timed = {k: v for k, v in prof.items() if v["n_timed"] > 0}
+    dom = max(timed, key=lambda k: timed[k]["ms"])
     d = prof[dom]
     avg_s = d["ms"] / d["n_timed"] / 1e3
-    fl = kernel_flops(dom, M, W, p, precision)
-    if fl is None:
+    share = d["ms"] / sum(v["ms"] for v in timed.values())
+    model = kernel_model(dom, M, W, precision)
+    if model is None:
         return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
-                "traffic": None}
+                "traffic": None, "avg_launch_ms": avg_s * 1e3, "share_of_step": share}
+    fl, bound, peak, src = model
     ach = fl / avg_s / 1e12
-    return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "FP64 FMA pipe derived from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-            "avg_launch_ms": avg_s * 1e3, "share_of_step": d["ms"] / sum(v["ms"] for v in prof.values())}
+    return {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": src, "avg_launch_ms": avg_s * 1e3, "share_of_step": share}
 
 
 # ---------------------------------------------------------------- ours
+def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barrier, max_over_ranks,
+                 with_e2e=True, with_clocks=None):
+    c = dict(WORKLOADS[WORKLOAD])
+    stab, p_order = 5, 6
+    stream = torch.cuda.current_stream(dev)
+    prec = ftq.FTQ_FP64 if precision == "fp64" else ftq.FTQ_MIXED
+    prop = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, stabilise_every=stab,
+                          exp_order=p_order, precision=prec, stream=stream)
+    M, na, n = prop.M, prop.n_alpha, prop.n_slices
+    total = warmup + steps
+    if total * stab > n:
+        raise SystemExit(f"warmup + steps must cover at most {n // stab} blocks of {stab} slices")
+    seed = c["seed"] + 1000 * rank
+    host = gaussian_fields(seed, total * stab, W, na).reshape(total, stab, W, na)
+    fields = torch.from_numpy(host).to(dev)
+    out = {"M": M, "n_slices": n, "dtau": prop.query_f64("DTAU"), "walkers": W, "stab": stab, "p": p_order}
+
+    for s in range(warmup):
+        prop.propagate(fields[s])
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches0 = prop.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(dev.index) if with_clocks else None
+    if clk:
+        clk.__enter__()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for s in range(warmup, total):
+        prop.propagate(fields[s])
+    est = prop.estimators(per_walker=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if clk:
+        clk.__exit__()
+        out["clocks"] = clk.summary()
+    barrier()
+    out["gpu_launches"] = prop.launches() - launches0
+    t_ms = max_over_ranks(e0.elapsed_time(e1))
+    out["ms_per_step"] = t_ms / steps
+    out["value"] = world * W * stab * steps / (t_ms / 1e3)
+    out["estimate"] = {"E_per_electron": est["E"].real / c["N"], "N": est["N"].real, "alive": est["n_alive"]}
+
+    if with_e2e:
+        pinned = torch.from_numpy(host).pin_memory()
+        staging = torch.empty((stab, W, na), dtype=torch.float64, device=dev)
+        wbuf = torch.empty((W, 8), dtype=torch.float64, device=dev)
+        wpin = torch.empty((W, 8), dtype=torch.float64).pin_memory()
+        prop.reset()
+        for s in range(warmup):
+            staging.copy_(pinned[s], non_blocking=True)
+            prop.propagate(staging)
+        torch.cuda.synchronize(dev)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for s in range(warmup, total):
+            staging.copy_(pinned[s], non_blocking=True)
+            prop.propagate(staging)
+            prop.lib.ftq_weights(prop.h, ctypes.c_void_p(wbuf.data_ptr()))
+            wpin.copy_(wbuf, non_blocking=True)
+        prop.estimators(per_walker=False)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        te_ms = max_over_ranks(f0.elapsed_time(f1))
+        out["e2e"] = {"value": world * W * stab * steps / (te_ms / 1e3), "unit": "walker-slices/s",
+                      "h2d_bytes_per_step": int(stab * W * na * 8), "d2h_bytes_per_step": int(W * 8 * 8),
+                      "note": "fields copied from pinned host memory and per-walker weights read back every "
+                              "step, one estimator read-back per timed run"}
+
+    # per-kernel launch durations: CUDA events on the launching stream, one block
+    prop.reset()
+    prop.propagate(fields[0])
+    before = prop.profile_read()
+    prop.profile(True)
+    prop.propagate(fields[1])
+    prop.estimators(per_walker=False)
+    after = prop.profile_read()
+    prop.profile(False)
+    prof = {k: {"ms": after[k][0], "n_timed": after[k][1] - before[k][1]} for k in after}
+    out["kernel_ms_per_step"] = {k: v["ms"] for k, v in prof.items() if v["ms"] > 0}
+    out["roofline"] = roofline(prof, M, W, precision)
+    out["device_status"] = prop.status()
+    prop.close()
+    return out
+
+
+def accuracy_vs_fp64(ftq, torch, dev, W=32):
+    """E/N at tau = beta of the mixed and the complex128 path on identical
+    fields (whole path, W walkers)."""
+    c = dict(WORKLOADS[WORKLOAD])
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, prec in (("fp64", ftq.FTQ_FP64), ("mixed", ftq.FTQ_MIXED)):
+        prop = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, stabilise_every=5,
+                              exp_order=6, precision=prec, stream=stream)
+        n = prop.n_slices
+        f = torch.from_numpy(gaussian_fields(c["seed"] + 777, n, W, prop.n_alpha)).to(dev)
+        t0 = time.perf_counter()
+        prop.propagate(f)
+        est = prop.estimators(per_walker=True)
+        pw = est["per_walker"].cpu().numpy()
+        res[name] = {"E_per_electron": est["E"].real / c["N"], "N": est["N"].real, "alive": est["n_alive"],
+                     "seconds": time.perf_counter() - t0, "alive_mask": (pw[:, 2] > 0.5).tolist(),
+                     "status": prop.status()}
+        prop.close()
+    d = abs(res["mixed"]["E_per_electron"] - res["fp64"]["E_per_electron"])
+    return {"E_per_electron_abs_diff": d, "bound": 1e-5, "within_bound": d <= 1e-5,
+            "E_per_electron_fp64": res["fp64"]["E_per_electron"], "E_per_electron_mixed": res["mixed"]["E_per_electron"],
+            "N_fp64": res["fp64"]["N"], "N_mixed": res["mixed"]["N"],
+            "same_killed_walkers": res["fp64"]["alive_mask"] == res["mixed"]["alive_mask"],
+            "walkers": W, "slices": 348, "fields": "seeded N(0,1), identical for both paths"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import __graft_entry__
@@ -178,23 +307,6 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     c = dict(WORKLOADS[WORKLOAD])
     W = args.walkers or c["walkers"]
-    stab = 5
-    p_order = 6
-    prec = ftq.FTQ_FP64 if args.precision == "fp64" else ftq.FTQ_MIXED
-    stream = torch.cuda.current_stream(dev)
-    prop = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, stabilise_every=stab,
-                          exp_order=p_order, precision=prec, stream=stream)
-    M, na, n = prop.M, prop.n_alpha, prop.n_slices
-    steps_total = args.warmup + args.steps
-    if steps_total * stab > n:
-        raise SystemExit(f"warmup + steps must cover at most {n // stab} blocks of {stab} slices")
-    seed = c["seed"] + 1000 * rank
-    host = gaussian_fields(seed, steps_total * stab, W, na).reshape(steps_total, stab, W, na)
-    fields = torch.from_numpy(host).to(dev)
-    pinned = torch.from_numpy(host).pin_memory()
-    staging = torch.empty((stab, W, na), dtype=torch.float64, device=dev)
-    wbuf = torch.empty((W, 8), dtype=torch.float64, device=dev)
-    wpin = torch.empty((W, 8), dtype=torch.float64).pin_memory()
 
     def barrier():
         if world > 1:
@@ -209,85 +321,45 @@ def run_ours(args, rank, world, local_rank):
             return float(t.item())
         return x
 
-    # ---- device-resident inputs (value)
-    for s in range(args.warmup):
-        prop.propagate(fields[s])
-    torch.cuda.synchronize(dev)
-    barrier()
-    launches0 = prop.launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for s in range(args.warmup, steps_total):
-            prop.propagate(fields[s])
-        est = prop.estimators(per_walker=False)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-    barrier()
-    launches = prop.launches() - launches0
-    t_ms = max_over_ranks(e0.elapsed_time(e1))
-    ws_per_step = W * stab
-    value = world * ws_per_step * args.steps / (t_ms / 1e3)
-
-    # ---- end to end through the public API with host buffers
-    prop.reset()
-    for s in range(args.warmup):
-        staging.copy_(pinned[s], non_blocking=True)
-        prop.propagate(staging)
-    torch.cuda.synchronize(dev)
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for s in range(args.warmup, steps_total):
-        staging.copy_(pinned[s], non_blocking=True)
-        prop.propagate(staging)
-        prop.lib.ftq_weights(prop.h, __import__("ctypes").c_void_p(wbuf.data_ptr()))
-        wpin.copy_(wbuf, non_blocking=True)
-    est2 = prop.estimators(per_walker=False)
-    f1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
-    te_ms = max_over_ranks(f0.elapsed_time(f1))
-    e2e_value = world * ws_per_step * args.steps / (te_ms / 1e3)
-
-    # ---- per-kernel launch durations (CUDA events on the launching stream)
-    prop.reset()
-    prop.propagate(fields[0])
-    before = prop.profile_read()
-    prop.profile(True)
-    prop.propagate(fields[1])
-    prop.estimators(per_walker=False)
-    after = prop.profile_read()
-    prop.profile(False)
-    prof = {k: {"ms": after[k][0], "n_timed": after[k][1] - before[k][1]} for k in after}
-    rl = roofline(prof, M, W, p_order, args.precision)
-    status = prop.status()
-    dtau = prop.query_f64("DTAU")
-    prop.close()
+    head = measure_path(ftq, torch, dev, args.precision, W, args.steps, args.warmup, world, rank, barrier,
+                        max_over_ranks, with_e2e=True, with_clocks=True)
+    comparison = None
+    if args.precision == "mixed" and not args.no_compare:
+        comparison = measure_path(ftq, torch, dev, "fp64", W, args.fp64_steps, args.warmup, world, rank, barrier,
+                                  max_over_ranks, with_e2e=False, with_clocks=False)
+    acc = None
+    if args.precision == "mixed" and not args.no_accuracy and rank == 0:
+        acc = accuracy_vs_fp64(ftq, torch, dev)
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": value, "unit": "walker-slices/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64(3xtf32)+c128",
+        "metric": METRIC, "value": head["value"], "unit": "walker-slices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if args.precision == "fp64" else "c64(tf32 hi+lo)+c128",
         "data": "synthetic: seeded N(0,1) Philox fields; UEG tables from (N, M, r_s, Theta, dtau)",
-        "config": {"workload": WORKLOAD, "N": c["N"], "M": M, "rs": c["rs"], "theta": c["theta"],
-                   "dtau": dtau, "n_slices": n, "walkers": W,
-                   "slices_per_step": stab, "exp_order": p_order, "precision": args.precision,
+        "config": {"workload": WORKLOAD, "N": c["N"], "M": head["M"], "rs": c["rs"], "theta": c["theta"],
+                   "dtau": head["dtau"], "n_slices": head["n_slices"], "walkers": W,
+                   "slices_per_step": head["stab"], "exp_order": head["p"], "precision": args.precision,
                    "step": "one stabilisation block (5 slices) for all walkers; one estimator call per timed run",
-                   "l2": "inputs larger than L2: walker state %.1f GB per rank" % (W * 7 * M * M * 16 / 1e9),
+                   "l2": "inputs larger than L2: walker state > 7 GB per rank",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": rl,
-        "e2e": {"value": e2e_value, "unit": "walker-slices/s",
-                "h2d_bytes_per_step": int(stab * W * na * 8), "d2h_bytes_per_step": int(W * 8 * 8),
-                "note": "fields copied from pinned host memory and per-walker weights read back every step"},
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
-        "kernel_ms_per_step": {k: v["ms"] for k, v in prof.items() if v["ms"] > 0},
-        "estimate": {"E_per_electron": (est["E"].real / c["N"]), "N": est["N"].real, "alive": est["n_alive"]},
-        "device_status": status,
+        "roofline": head["roofline"],
+        "e2e": head["e2e"],
+        "gpu_launches": int(head["gpu_launches"]),
+        "clocks": head.get("clocks"),
+        "kernel_ms_per_step": head["kernel_ms_per_step"],
+        "estimate": head["estimate"],
+        "device_status": head["device_status"],
     }
+    if comparison:
+        line["fp64_path"] = {"value": comparison["value"], "ms_per_step": comparison["ms_per_step"],
+                             "steps": args.fp64_steps, "warmup": args.warmup,
+                             "speedup_mixed_over_fp64": head["value"] / comparison["value"],
+                             "roofline": comparison["roofline"],
+                             "kernel_ms_per_step": comparison["kernel_ms_per_step"]}
+    if acc:
+        line["error_vs_fp64"] = acc
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

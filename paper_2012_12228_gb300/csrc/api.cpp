@@ -38,6 +38,7 @@ cudaError_t upload(ftq_ctx* c, T** p, const std::vector<T>& v) {
 
 void free_all(ftq_ctx* c) {
     void* ptrs[] = {c->Y, c->Tinv, c->G, c->work, c->work2, c->zbuf[0], c->zbuf[1], c->DR, c->phi,
+                    c->Ypl, c->zpl[0], c->zpl[1], c->G32, c->w32, c->w2_32,
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0};
@@ -73,10 +74,6 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         delete c;
         return fail(nullptr, FTQ_EINVAL, "M > 1024 is not supported by the per-walker factorisation kernels");
     }
-    if (opts->precision == FTQ_MIXED) {
-        delete c;
-        return fail(nullptr, FTQ_EINVAL, "FTQ_MIXED is not available in this build");
-    }
     c->opts = *opts;
     c->stream = reinterpret_cast<cudaStream_t>(opts->cuda_stream);
     c->W = opts->walkers;
@@ -85,7 +82,19 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     const size_t W = c->W, MM = (size_t)M * M;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    chk(dalloc(c, &c->Y, W * MM));
+    if (opts->precision == FTQ_FP64) {
+        chk(dalloc(c, &c->Y, W * MM));
+    } else {
+        c->Kp = (M + 7) / 8 * 8;
+        c->LD = (M + 7) / 8 * 8;
+        const size_t wsz = 4 * (size_t)c->Kp * c->LD;
+        chk(dalloc(c, &c->Ypl, W * wsz));
+        chk(dalloc(c, &c->zpl[0], W * wsz));
+        chk(dalloc(c, &c->zpl[1], W * wsz));
+        chk(dalloc(c, &c->G32, W * MM));
+        chk(dalloc(c, &c->w32, W * MM));
+        chk(dalloc(c, &c->w2_32, W * MM));
+    }
     chk(dalloc(c, &c->Tinv, W * MM));
     chk(dalloc(c, &c->G, W * MM));
     chk(dalloc(c, &c->work, W * MM));

@@ -83,22 +83,26 @@ __global__ void k_init_walkers(double2* DR, double* ws, int M, int W, double ld0
 // rho_Q = -sum G[b][a].  <v_A> = 2 i c (rho_Q + rho_-Q), <v_B> = -2 c (rho_Q -
 // rho_-Q); xbar = -sqrt(dtau) <v>; y = x - xbar; the V generator
 // phi(+Q) = sqrt(dtau) c i (y_A + i y_B), phi(-Q) = sqrt(dtau) c i (y_A - i y_B).
-__global__ void k_force_bias(const double2* __restrict__ G, const double* __restrict__ x,
+__device__ __forceinline__ double2 to_c128(double2 v) { return v; }
+__device__ __forceinline__ double2 to_c128(float2 v) { return make_double2(v.x, v.y); }
+
+template <typename GT>
+__global__ void k_force_bias(const GT* __restrict__ G, const double* __restrict__ x,
                              double2* __restrict__ phi, double* __restrict__ ws,
                              const int* __restrict__ pptr, const int* __restrict__ pa,
                              const int* __restrict__ pb, const double* __restrict__ cq,
                              int M, int nqh, double sdt) {
     __shared__ double2 sh[32];
     const int w = blockIdx.x;
-    const double2* Gw = G + (long)w * M * M;
+    const GT* Gw = G + (long)w * M * M;
     const double* xw = x + (long)w * 2 * nqh;
     double2* ph = phi + (long)w * (2 * nqh + 1);
     double2 gauss = make_double2(0.0, 0.0);
     if (threadIdx.x == 0) ph[0] = make_double2(0.0, 0.0);
     for (int q = threadIdx.x; q < nqh; q += blockDim.x) {
         double2 rp = make_double2(0.0, 0.0), rm = make_double2(0.0, 0.0);
-        for (int e = pptr[1 + 2 * q]; e < pptr[2 + 2 * q]; ++e) rp = rp - Gw[(long)pb[e] * M + pa[e]];
-        for (int e = pptr[2 + 2 * q]; e < pptr[3 + 2 * q]; ++e) rm = rm - Gw[(long)pb[e] * M + pa[e]];
+        for (int e = pptr[1 + 2 * q]; e < pptr[2 + 2 * q]; ++e) rp = rp - to_c128(Gw[(long)pb[e] * M + pa[e]]);
+        for (int e = pptr[2 + 2 * q]; e < pptr[3 + 2 * q]; ++e) rm = rm - to_c128(Gw[(long)pb[e] * M + pa[e]]);
         const double c = cq[q];
         double2 vA = times_i((rp + rm) * (2.0 * c));
         double2 vB = (rp - rm) * (-2.0 * c);
@@ -552,22 +556,37 @@ cudaError_t launch_init_walkers(ftq_ctx* c) {
     for (int i = 0; i < M; ++i) ld0 += std::log1p(std::exp(-c->sys.beta * (c->sys.eps[i] - c->sys.mu_T)));
     long total = (long)W * M * M;
     LaunchScope ls0(c, FTQ_K_INIT);
-    k_init_matrices<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(c->Y, c->Tinv, c->G, c->tab.g0, M, total);
+    k_init_matrices<<<(unsigned)((total + 255) / 256), 256, 0, c->stream>>>(c->Y ? c->Y : c->zbuf[1], c->Tinv, c->G,
+                                                                           c->tab.g0, M, total);
     c->launches[FTQ_K_INIT] += 1;
     k_init_walkers<<<W, 64, 0, c->stream>>>(c->DR, c->wstate, M, W, ld0);
     c->k = 0;
+    c->g64_valid = true;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && c->opts.precision == FTQ_MIXED) e = mixed_init(c);
+    return e;
+}
+
+cudaError_t launch_force_bias_any(ftq_ctx* c, const double* x, const void* G, bool g32) {
+    LaunchScope ls(c, FTQ_K_FORCE_BIAS);
+    if (g32)
+        k_force_bias<float2><<<c->W, 256, 0, c->stream>>>(reinterpret_cast<const float2*>(G), x, c->phi, c->wstate,
+                                                          c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.cq,
+                                                          c->M, c->sys.nq_half, std::sqrt(c->sys.dtau));
+    else
+        k_force_bias<double2><<<c->W, 256, 0, c->stream>>>(reinterpret_cast<const double2*>(G), x, c->phi,
+                                                           c->wstate, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b,
+                                                           c->tab.cq, c->M, c->sys.nq_half, std::sqrt(c->sys.dtau));
     return cudaGetLastError();
 }
 
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x) {
-    LaunchScope ls(c, FTQ_K_FORCE_BIAS);
-    k_force_bias<<<c->W, 256, 0, c->stream>>>(c->G, x, c->phi, c->wstate, c->tab.pair_ptr, c->tab.pair_a,
-                                              c->tab.pair_b, c->tab.cq, c->M, c->sys.nq_half,
-                                              std::sqrt(c->sys.dtau));
-    return cudaGetLastError();
+    if (c->opts.precision == FTQ_MIXED && c->k > 0) return launch_force_bias_any(c, x, c->G32, true);
+    return launch_force_bias_any(c, x, c->G, false);
 }
 
 cudaError_t launch_chain(ftq_ctx* c) {
+    if (c->opts.precision == FTQ_MIXED) return mixed_chain(c);
     const int M = c->M, p = c->opts.exp_order;
     const int tiles = (M + CT - 1) / CT;
     dim3 grid(tiles * tiles, c->W);
@@ -590,35 +609,48 @@ cudaError_t launch_chain(ftq_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_qrcp(ftq_ctx* c) {
+cudaError_t launch_qrcp64(ftq_ctx* c, const double2* Yin, double2* Qout) {
     const int M = c->M;
     size_t sm = sizeof(double) * M + sizeof(int) * M;
     int nt = fact_threads(M);
-    {
     LaunchScope ls(c, FTQ_K_QRCP);
-    k_qrcp<<<c->W, nt, sm, c->stream>>>(c->Y, c->zbuf[0], c->work, c->work2, c->DR, c->Tinv, c->hh, c->htau,
+    k_qrcp<<<c->W, nt, sm, c->stream>>>(Yin, Qout, c->work, c->work2, c->DR, c->Tinv, c->hh, c->htau,
                                        c->wstate, c->status, M);
-    }
-    double2* q = c->zbuf[0];
-    c->zbuf[0] = c->Y;
-    c->Y = q;
     return cudaGetLastError();
 }
 
-cudaError_t launch_green(ftq_ctx* c, int k, bool update) {
+cudaError_t launch_qrcp(ftq_ctx* c) {
+    if (c->opts.precision == FTQ_MIXED) return mixed_qrcp(c);
+    cudaError_t e = launch_qrcp64(c, c->Y, c->zbuf[0]);
+    double2* q = c->zbuf[0];
+    c->zbuf[0] = c->Y;
+    c->Y = q;
+    return e;
+}
+
+cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update) {
     const int M = c->M;
     size_t sm = (2 * sizeof(double2) + 3 * sizeof(double) + sizeof(int)) * M;
     int nt = fact_threads(M);
     double lscale = (double)(c->sys.n_slices - k) * c->sys.dtau;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     LaunchScope ls(c, FTQ_K_GREEN);
-    k_green<<<c->W, nt, sm, c->stream>>>(c->Y, c->Tinv, c->DR, c->work, c->work2, c->G, c->tab.eps, c->wstate,
+    k_green<<<c->W, nt, sm, c->stream>>>(Y, c->Tinv, c->DR, c->work, c->work2, c->G, c->tab.eps, c->wstate,
                                         c->status, M, lscale, c->sys.mu_T, c->opts.constraint, update ? 1 : 0);
     return cudaGetLastError();
 }
 
+cudaError_t launch_green(ftq_ctx* c, int k, bool update) {
+    if (c->opts.precision == FTQ_MIXED) return mixed_green(c, k);
+    return launch_green64(c, c->Y, k, update);
+}
+
 cudaError_t launch_estimators(ftq_ctx* c, double* per_walker) {
     const int M = c->M, nqh = c->sys.nq_half;
+    if (!c->g64_valid) {
+        cudaError_t e0 = mixed_sync_g64(c);
+        if (e0 != cudaSuccess) return e0;
+    }
     size_t sm = sizeof(double2) * (2 * nqh + 1);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_estimators, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     LaunchScope ls(c, FTQ_K_ESTIMATORS);
@@ -635,6 +667,10 @@ cudaError_t launch_estimators(ftq_ctx* c, double* per_walker) {
 }
 
 cudaError_t launch_copy_green(ftq_ctx* c, double2* out) {
+    if (!c->g64_valid) {
+        cudaError_t e0 = mixed_sync_g64(c);
+        if (e0 != cudaSuccess) return e0;
+    }
     return cudaMemcpyAsync(out, c->G, sizeof(double2) * (size_t)c->W * c->M * c->M, cudaMemcpyDeviceToDevice,
                            c->stream);
 }

@@ -58,12 +58,21 @@ struct ftq_ctx {
     int W = 0, M = 0, k = 0;
     int nslot = 0;                // 2 nq_half + 1
     // walker state (complex128 unless noted)
-    double2* Y = nullptr;         // chain: B's since the last QRCP times Q_R   [W][M][M]
+    double2* Y = nullptr;         // FP64 chain: B's since the last QRCP times Q_R [W][M][M]
     double2* Tinv = nullptr;      // T_R^-1                                   [W][M][M]
-    double2* G = nullptr;         // G(tau_k)                                 [W][M][M]
+    double2* G = nullptr;         // G(tau_k), complex128                     [W][M][M]
     double2* work = nullptr;      // LU / QR workspace                        [W][M][M]
     double2* work2 = nullptr;     // triangular-solve workspace (column-major)[W][M][M]
-    double2* zbuf[2] = {nullptr, nullptr};   // Horner buffers                [W][M][M]
+    double2* zbuf[2] = {nullptr, nullptr};   // Horner buffers (FP64) / FP64 bridges (mixed)
+    // mixed precision: the chain in FP32 planes split hi + lo for 3xTF32,
+    // per walker [hi re | hi im | lo re | lo im], each Kp x LD, zero padded
+    int Kp = 0, LD = 0;
+    float* Ypl = nullptr;
+    float* zpl[2] = {nullptr, nullptr};
+    float2* G32 = nullptr;        // G(tau_k) for k < n, complex64            [W][M][M]
+    float2* w32 = nullptr;        // FP32 LU workspace                        [W][M][M]
+    float2* w2_32 = nullptr;      // FP32 solve workspace                     [W][M][M]
+    bool g64_valid = true;        // G holds the current G(tau) (mixed: only at k = 0, n)
     double2* DR = nullptr;        // D_R                                       [W][M]
     double2* phi = nullptr;       // V generator table per walker              [W][nslot]
     double2* hh = nullptr;        // Householder u_0 per column                [W][M]
@@ -128,5 +137,16 @@ cudaError_t launch_qrcp(ftq_ctx* c);
 cudaError_t launch_green(ftq_ctx* c, int k, bool update_weights);
 cudaError_t launch_estimators(ftq_ctx* c, double* per_walker);
 cudaError_t launch_copy_green(ftq_ctx* c, double2* out);
+// complex128 factorisations on explicit buffers
+cudaError_t launch_qrcp64(ftq_ctx* c, const double2* Yin, double2* Qout);
+cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update_weights);
+cudaError_t launch_force_bias_any(ftq_ctx* c, const double* x, const void* G, bool g32);
+
+// Mixed-precision launchers (mixed_kernels.cu).
+cudaError_t mixed_init(ftq_ctx* c);
+cudaError_t mixed_chain(ftq_ctx* c);
+cudaError_t mixed_qrcp(ftq_ctx* c);
+cudaError_t mixed_green(ftq_ctx* c, int k);
+cudaError_t mixed_sync_g64(ftq_ctx* c);    // make G (complex128) hold G(tau) now
 
 }  // namespace ftq

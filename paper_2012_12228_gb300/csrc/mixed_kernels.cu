@@ -1,0 +1,466 @@
+// Mixed-precision slice path: the B chain held in FP32 planes split into
+// tf32 hi + lo parts (the operand format of 3xTF32 tensor-core products),
+// G(tau) and ln det per slice from an FP32 LU with FP64 log accumulation,
+// and bridges to the complex128 QRCP (every s slices) and to the complex128
+// G(beta) used by the estimators.
+#include <cmath>
+
+#include "complex_math.cuh"
+#include "ftq_internal.h"
+
+namespace ftq {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// v ~= hi + lo with hi, lo both tf32 values (|v - hi - lo| <= 2^-22 |v|)
+__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
+    hi = tf32_rna(v);
+    lo = tf32_rna(v - hi);
+}
+
+struct Planes {
+    size_t plane;    // Kp * LD
+    int LD;
+    __device__ __forceinline__ float2 load(const float* w, int i, int c) const {
+        size_t o = (size_t)i * LD + c;
+        return make_float2(w[o] + w[2 * plane + o], w[plane + o] + w[3 * plane + o]);
+    }
+    __device__ __forceinline__ void store(float* w, int i, int c, float2 v) const {
+        size_t o = (size_t)i * LD + c;
+        float h, l;
+        split_tf32(v.x, h, l);
+        w[o] = h;
+        w[2 * plane + o] = l;
+        split_tf32(v.y, h, l);
+        w[plane + o] = h;
+        w[3 * plane + o] = l;
+    }
+};
+
+template <typename T>
+__device__ T block_sum(T v, T* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = v + shfl_down(v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T acc = sh[0];
+        for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i) acc = acc + sh[i];
+        sh[0] = acc;
+    }
+    __syncthreads();
+    T r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ int block_argmax(float val, int idx, float* shv, int* shi) {
+    for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_down_sync(0xffffffffu, val, o);
+        int oi = __shfl_down_sync(0xffffffffu, idx, o);
+        if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { shv[wid] = val; shi[wid] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float bv = shv[0];
+        int bi = shi[0];
+        for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i)
+            if (shv[i] > bv || (shv[i] == bv && shi[i] < bi)) { bv = shv[i]; bi = shi[i]; }
+        shi[0] = bi;
+    }
+    __syncthreads();
+    int r = shi[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------- layout bridges
+__global__ void k_planes_identity(float* Ypl, size_t plane, int LD, int M, size_t wstride, int W) {
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= (long)W * M) return;
+    int w = (int)(e / M), i = (int)(e % M);
+    Ypl[wstride * w + (size_t)i * LD + i] = 1.0f;
+}
+
+__global__ void k_planes_to_c128(const float* __restrict__ Ypl, double2* __restrict__ Y, size_t plane, int LD,
+                                 int M, size_t wstride, long total) {
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    long w = e / ((long)M * M);
+    int ij = (int)(e % ((long)M * M));
+    int i = ij / M, c = ij % M;
+    const float* p = Ypl + wstride * w;
+    size_t o = (size_t)i * LD + c;
+    Y[e] = make_double2((double)p[o] + (double)p[2 * plane + o], (double)p[plane + o] + (double)p[3 * plane + o]);
+}
+
+__global__ void k_c128_to_planes(const double2* __restrict__ Y, float* __restrict__ Ypl, size_t plane, int LD,
+                                 int M, size_t wstride, long total) {
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    long w = e / ((long)M * M);
+    int ij = (int)(e % ((long)M * M));
+    int i = ij / M, c = ij % M;
+    float* p = Ypl + wstride * w;
+    size_t o = (size_t)i * LD + c;
+    double2 v = Y[e];
+    // hi = tf32(v), lo = tf32(v - hi) computed in double so the pair keeps ~22 bits
+    float h = tf32_rna((float)v.x);
+    p[o] = h;
+    p[2 * plane + o] = tf32_rna((float)(v.x - (double)h));
+    h = tf32_rna((float)v.y);
+    p[plane + o] = h;
+    p[3 * plane + o] = tf32_rna((float)(v.y - (double)h));
+}
+
+__global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict__ b, long total) {
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    float2 v = a[e];
+    b[e] = make_double2(v.x, v.y);
+}
+
+__global__ void k_g32_init(float2* G, const double* g0, int M, long total) {
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int ij = (int)(e % ((long)M * M));
+    int i = ij / M, j = ij % M;
+    G[e] = make_float2(i == j ? (float)g0[i] : 0.0f, 0.0f);
+}
+
+// ---------------------------------------------------------------- FP32 chain (CUDA cores)
+// out = os (us Y + alpha V (zs Z)) on the split planes; V gathered from phi.
+constexpr int ST = 64;   // output tile (complex)
+constexpr int SK = 16;   // k tile
+
+__global__ void __launch_bounds__(256) k_chain32(const float* __restrict__ Zin, const float* __restrict__ Yu,
+                                                float* __restrict__ out, const double2* __restrict__ phi,
+                                                const uint16_t* __restrict__ vidx, const double* __restrict__ zs,
+                                                const double* __restrict__ us, const double* __restrict__ os,
+                                                float alpha, int M, int nslot, int tiles, Planes P, size_t wstride) {
+    __shared__ float2 As[SK][ST + 1];
+    __shared__ float2 Bs[SK][ST + 1];
+    const int w = blockIdx.y;
+    const int ti = blockIdx.x / tiles, tj = blockIdx.x % tiles;
+    const int r0 = ti * ST, c0 = tj * ST;
+    const float* Z = Zin + wstride * w;
+    const double2* ph = phi + (long)w * nslot;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < M; k0 += SK) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            int e = threadIdx.x + 256 * l;          // 0..1023
+            int r = e >> 4, kk = e & 15;            // A: 64 rows x 16 k
+            int i = r0 + r, k = k0 + kk;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < M && k < M) {
+                double2 d = ph[vidx[(long)i * M + k]];
+                double s = zs ? zs[k] : 1.0;
+                v = make_float2((float)(d.x * s), (float)(d.y * s));
+            }
+            As[kk][r] = v;
+            int kb = e >> 6, cb = e & 63;           // B: 16 k x 64 cols
+            int kr = k0 + kb, cc = c0 + cb;
+            float2 z = make_float2(0.f, 0.f);
+            if (kr < M && cc < M) z = P.load(Z, kr, cc);
+            Bs[kb][cb] = z;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < SK; ++kk) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { a[q] = As[kk][ty + 16 * q]; b[q] = Bs[kk][tx + 16 * q]; }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = cfma(a[x], b[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+    float* O = out + wstride * w;
+    const float* U = Yu + wstride * w;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int i = r0 + ty + 16 * a, c = c0 + tx + 16 * b;
+            if (i < M && c < M) {
+                float2 u = P.load(U, i, c);
+                float s = (float)us[i];
+                float2 v = make_float2(u.x * s + alpha * acc[a][b].x, u.y * s + alpha * acc[a][b].y);
+                if (os) { float o = (float)os[i]; v.x *= o; v.y *= o; }
+                P.store(O, i, c, v);
+            }
+        }
+}
+
+// ---------------------------------------------------------------- FP32 G(tau) + ln det
+// Same algebra as the complex128 kernel: Mt = D_Lb T^-1 D_Rb + D_Ls Y D_Rs in
+// FP32, LU with partial pivoting, G = I - Y D_Rs Mt^-1 D_Ls, ln det from the
+// pivots accumulated in FP64, weight update in FP64.
+__global__ void k_green32(const float* __restrict__ Ypl, const double2* __restrict__ Tinv,
+                          const double2* __restrict__ DR, float2* __restrict__ work, float2* __restrict__ work2,
+                          float2* __restrict__ G, const double* __restrict__ eps, double* __restrict__ ws,
+                          int* __restrict__ status, int M, double lscale, double mu_T, int constraint,
+                          Planes P, size_t wstride) {
+    extern __shared__ unsigned char smem_raw[];
+    float2* drs = reinterpret_cast<float2*>(smem_raw);      // [M]
+    float2* invU = drs + M;                                 // [M]
+    float* dls = reinterpret_cast<float*>(invU + M);        // [M]
+    float* dlb = dls + M;                                   // [M]
+    float* drb = dlb + M;                                   // [M]
+    int* perm = reinterpret_cast<int*>(drb + M);            // [M]
+    __shared__ float shv[32];
+    __shared__ int shi[32];
+    __shared__ double shd[32];
+    __shared__ double2 shc[32];
+    __shared__ int nswap;
+    const int w = blockIdx.x;
+    const long off = (long)w * M * M;
+    const int nt = blockDim.x;
+    float2* A = work + off;
+    float2* XT = work2 + off;
+    const float* Yw = Ypl + wstride * w;
+    const double2* Tw = Tinv + off;
+    float2* Gw = G + off;
+
+    double lsum = 0.0;
+    for (int i = threadIdx.x; i < M; i += nt) {
+        double dl = exp(-lscale * (eps[i] - mu_T));
+        double b, s2;
+        if (dl > 1.0) { b = 1.0 / dl; s2 = 1.0; } else { b = 1.0; s2 = dl; }
+        dlb[i] = (float)b; dls[i] = (float)s2;
+        double2 d = DR[(long)w * M + i];
+        double a = sqrt(abs2(d));
+        double rb;
+        double2 rs;
+        if (a > 1.0) { rb = 1.0 / a; rs = d * (1.0 / a); } else { rb = 1.0; rs = d; }
+        drb[i] = (float)rb;
+        drs[i] = make_float2((float)rs.x, (float)rs.y);
+        lsum += log(b) + log(rb);
+        perm[i] = i;
+    }
+    if (threadIdx.x == 0) nswap = 0;
+    __syncthreads();
+    for (long e = threadIdx.x; e < (long)M * M; e += nt) {
+        int i = (int)(e / M), j = (int)(e % M);
+        double2 t = Tw[e] * ((double)dlb[i] * (double)drb[j]);
+        float2 y = cmul(P.load(Yw, i, j), drs[j]) * dls[i];
+        A[e] = make_float2((float)t.x + y.x, (float)t.y + y.y);
+    }
+    __syncthreads();
+    for (int j = 0; j < M; ++j) {
+        float best = -1.0f;
+        int bidx = M;
+        for (int i = j + threadIdx.x; i < M; i += nt) {
+            float2 v = A[(long)i * M + j];
+            float a1 = fabsf(v.x) + fabsf(v.y);
+            if (a1 > best) { best = a1; bidx = i; }
+        }
+        int p = block_argmax(best, bidx, shv, shi);
+        if (p >= M) {
+            p = j;
+            if (threadIdx.x == 0) atomicOr(status, 1);
+        }
+        if (p != j) {
+            for (int c = threadIdx.x; c < M; c += nt) {
+                float2 t = A[(long)j * M + c];
+                A[(long)j * M + c] = A[(long)p * M + c];
+                A[(long)p * M + c] = t;
+            }
+            if (threadIdx.x == 0) {
+                int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+                nswap ^= 1;
+            }
+        }
+        __syncthreads();
+        const float2 piv = A[(long)j * M + j];
+        const float n2 = piv.x * piv.x + piv.y * piv.y;
+        if (!(n2 > 0.0f) && threadIdx.x == 0) atomicOr(status, 1);
+        const float2 ip = make_float2(piv.x / n2, -piv.y / n2);
+        for (int i = j + 1 + threadIdx.x; i < M; i += nt) A[(long)i * M + j] = cmul(A[(long)i * M + j], ip);
+        if (threadIdx.x == 0) invU[j] = ip;
+        __syncthreads();
+        for (int c = j + 1 + threadIdx.x; c < M; c += nt) {
+            const float2 u = A[(long)j * M + c];
+            for (int i = j + 1; i < M; ++i) A[(long)i * M + c] = A[(long)i * M + c] - cmul(A[(long)i * M + j], u);
+        }
+        __syncthreads();
+    }
+    double2 ldm = make_double2(0.0, 0.0);
+    for (int j = threadIdx.x; j < M; j += nt) {
+        float2 u = A[(long)j * M + j];
+        double ux = u.x, uy = u.y;
+        ldm = ldm + make_double2(0.5 * log(ux * ux + uy * uy), atan2(uy, ux));
+    }
+    ldm = block_sum(ldm, shc);
+    lsum = block_sum(lsum, shd);
+    for (int i = threadIdx.x; i < M; i += nt) {
+        for (int j = 0; j < M; ++j) {
+            float2 s = cmul(P.load(Yw, i, j), drs[j]);
+            for (int m = 0; m < j; ++m) s = s - cmul(XT[(long)m * M + i], A[(long)m * M + j]);
+            XT[(long)j * M + i] = cmul(s, invU[j]);
+        }
+        for (int j = M - 2; j >= 0; --j) {
+            float2 s = XT[(long)j * M + i];
+            for (int m = j + 1; m < M; ++m) s = s - cmul(XT[(long)m * M + i], A[(long)m * M + j]);
+            XT[(long)j * M + i] = s;
+        }
+        for (int m = 0; m < M; ++m) {
+            int c = perm[m];
+            float2 g = XT[(long)m * M + i] * (-dls[c]);
+            if (c == i) g.x += 1.0f;
+            Gw[(long)i * M + c] = g;
+        }
+    }
+    if (threadIdx.x == 0) {
+        double* s = ws + 8L * w;
+        double2 ld = ldm;
+        ld.x -= lsum;
+        ld.y += kPi * (double)(nswap ^ ((int)s[7]));
+        if (!isfinite(ld.x) || !isfinite(ld.y)) atomicOr(status, 1);
+        double2 lnS = make_double2(2.0 * (ld.x - s[3]), 2.0 * (ld.y - s[4]));
+        double gr = s[5], gi = s[6];
+        if (constraint == FTQ_FREE) {
+            s[0] += lnS.x + gr;
+            s[1] = remainder(s[1] + lnS.y + gi, 2.0 * kPi);
+        } else if (s[2] > 0.5) {
+            double cth = cos(lnS.y);
+            if (cth <= 0.0) s[2] = 0.0;
+            else s[0] += lnS.x + gr + log(cth);
+        }
+        s[3] = ld.x;
+        s[4] = remainder(ld.y, 2.0 * kPi);
+    }
+}
+
+int fact_threads(int M) {
+    int t = ((M + 31) / 32) * 32;
+    return t > 1024 ? 1024 : (t < 32 ? 32 : t);
+}
+
+Planes planes_of(const ftq_ctx* c) {
+    Planes P;
+    P.plane = (size_t)c->Kp * c->LD;
+    P.LD = c->LD;
+    return P;
+}
+
+size_t walker_stride(const ftq_ctx* c) { return 4 * (size_t)c->Kp * c->LD; }
+
+}  // namespace
+
+cudaError_t mixed_init(ftq_ctx* c) {
+    const int M = c->M, W = c->W;
+    const size_t ws = walker_stride(c);
+    cudaError_t e = cudaMemsetAsync(c->Ypl, 0, sizeof(float) * ws * W, c->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(c->zpl[b], 0, sizeof(float) * ws * W, c->stream);
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls(c, FTQ_K_INIT);
+        long n = (long)W * M;
+        k_planes_identity<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->Ypl, (size_t)c->Kp * c->LD, c->LD,
+                                                                             M, ws, W);
+    }
+    {
+        LaunchScope ls(c, FTQ_K_INIT);
+        long n = (long)W * M * M;
+        k_g32_init<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->G32, c->tab.g0, M, n);
+    }
+    c->g64_valid = true;
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_chain(ftq_ctx* c) {
+    const int M = c->M, p = c->opts.exp_order;
+    const int tiles = (M + ST - 1) / ST;
+    dim3 grid(tiles * tiles, c->W);
+    const Planes P = planes_of(c);
+    const size_t ws = walker_stride(c);
+    const float* zin = c->Ypl;
+    int cur = 0;
+    for (int j = p; j >= 1; --j) {
+        float* out = c->zpl[cur];
+        LaunchScope ls(c, FTQ_K_CHAIN);
+        k_chain32<<<grid, 256, 0, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, j == p ? c->tab.h : nullptr,
+                                               c->tab.h, j == 1 ? c->tab.h : nullptr, 1.0f / j, M, c->nslot, tiles,
+                                               P, ws);
+        zin = out;
+        cur ^= 1;
+    }
+    float* res = c->zpl[cur ^ 1];
+    c->zpl[cur ^ 1] = c->Ypl;
+    c->Ypl = res;
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_qrcp(ftq_ctx* c) {
+    const int M = c->M;
+    const long n = (long)c->W * M * M;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const size_t ws = walker_stride(c), plane = (size_t)c->Kp * c->LD;
+    double2* y64 = c->zbuf[1];
+    double2* q64 = c->zbuf[0];
+    {
+        LaunchScope ls(c, FTQ_K_QRCP);
+        k_planes_to_c128<<<blocks, 256, 0, c->stream>>>(c->Ypl, y64, plane, c->LD, M, ws, n);
+    }
+    cudaError_t e = launch_qrcp64(c, y64, q64);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(c, FTQ_K_QRCP);
+    k_c128_to_planes<<<blocks, 256, 0, c->stream>>>(q64, c->Ypl, plane, c->LD, M, ws, n);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_green(ftq_ctx* c, int k) {
+    const int M = c->M;
+    if (k == c->sys.n_slices) {
+        // tau = beta: the final G and ln det in complex128
+        const long n = (long)c->W * M * M;
+        {
+            LaunchScope ls(c, FTQ_K_GREEN);
+            k_planes_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+                c->Ypl, c->zbuf[1], (size_t)c->Kp * c->LD, c->LD, M, walker_stride(c), n);
+        }
+        cudaError_t e = launch_green64(c, c->zbuf[1], k, true);
+        c->g64_valid = true;
+        return e;
+    }
+    size_t sm = (2 * sizeof(float2) + 3 * sizeof(float) + sizeof(int)) * M;
+    int nt = fact_threads(M);
+    double lscale = (double)(c->sys.n_slices - k) * c->sys.dtau;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_green32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    LaunchScope ls(c, FTQ_K_GREEN);
+    k_green32<<<c->W, nt, sm, c->stream>>>(c->Ypl, c->Tinv, c->DR, c->w32, c->w2_32, c->G32, c->tab.eps, c->wstate,
+                                          c->status, M, lscale, c->sys.mu_T, c->opts.constraint, planes_of(c),
+                                          walker_stride(c));
+    c->g64_valid = false;
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_sync_g64(ftq_ctx* c) {
+    const long n = (long)c->W * c->M * c->M;
+    k_c64_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->G32, c->G, n);
+    c->launches[FTQ_K_ESTIMATORS] += 1;
+    c->g64_valid = true;
+    return cudaGetLastError();
+}
+
+}  // namespace ftq
