@@ -167,6 +167,34 @@ int ftq_profile(ftq_ctx* ctx, int enable);
  * Both arrays are host buffers of FTQ_K_COUNT entries; either may be NULL. */
 int ftq_profile_read(ftq_ctx* ctx, double* ms_host, int64_t* launches_host);
 
+/* Estimators without any device allocation (the paper has no counterpart;
+ * this is a service for callers that cannot let a library allocate device
+ * memory: applications whose device memory is owned by a framework pool
+ * with a fixed budget, and latency-sensitive loops that must not trigger the
+ * implicit device-wide synchronisation of cudaMalloc / cudaFree).
+ *
+ * Computes, for every walker w, the same per-walker values as
+ * ftq_estimators: N = 2 tr P and E = E_M + E_1 + E_2 from P = I - G_w^T for
+ * the UEG with N-bar = N electrons, M plane waves and Wigner-Seitz radius rs
+ * (the estimators do not depend on Theta, dtau or mu).
+ *   G_dev           device, complex128 [W][M][M] row-major (as ftq_green writes)
+ *   per_walker_dev  device float64 [W][8]: {0, 0, 1, Re E, Im E, Re N, Im N, 0}
+ *   cuda_stream     cudaStream_t to run on (NULL = legacy default stream)
+ * Working memory: the momentum-transfer tables are packed into one 4 MiB
+ * file-scope device array that every GPU which loads the library keeps until
+ * the process exits; bases whose tables do not fit (M above roughly 600)
+ * are rejected with FTQ_EINVAL and a message naming the size.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call rewrites the table region it uses
+ * and nothing in the array needs to start at zero.  All calls share the one
+ * array: calls that can overlap on the GPU (different streams, or different
+ * host threads on the same device) race and must be serialised by the
+ * caller.  Asynchronous on cuda_stream; errors via ftq_last_error(NULL). */
+int ftq_estimators_noalloc(int N, int M, double rs, const void* G_dev, int W,
+                           double* per_walker_dev, void* cuda_stream);
+
 /* Message of the last failure on ctx (or of the last failed ftq_init_ueg
  * when ctx is NULL).  Never NULL. */
 const char* ftq_last_error(const ftq_ctx* ctx);

@@ -31,8 +31,8 @@ class Opts(ctypes.Structure):
 
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
-           "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_last_error",
-           "ftq_destroy"]
+           "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc",
+           "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5}
 K_COUNT = 8
 
@@ -65,6 +65,7 @@ def load_library(path=None):
     lib.ftq_transfers.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.ftq_profile.argtypes = [vp, i]
     lib.ftq_profile_read.argtypes = [vp, dp, i64p]
+    lib.ftq_estimators_noalloc.argtypes = [i, i, d, vp, i, vp, vp]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]

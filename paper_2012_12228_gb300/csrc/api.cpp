@@ -48,6 +48,11 @@ void free_all(ftq_ctx* c) {
 
 }  // namespace
 
+namespace ftq {
+// Records a failure that is reported by ftq_last_error(NULL).
+void set_global_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace ftq
+
 extern "C" {
 
 int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu, double dtau,
