@@ -42,8 +42,11 @@ extern "C" {
 
 /* precision of the slice chain */
 #define FTQ_FP64   0      /* every step in complex128                                   */
-#define FTQ_MIXED  1      /* B chain in FP32-accurate tensor-core math, FP64 QR/UDT,
-                             FP64 determinants and weights                               */
+#define FTQ_MIXED  1      /* B chain in 3xTF32 tensor-core math (tcgen05, FP32 accumulate),
+                             FP32 per-slice G and LU, FP64 log-determinant accumulation,
+                             complex128 QR/UDT, G(beta) and log-weights                  */
+#define FTQ_MIXED_SIMT 2  /* as FTQ_MIXED with the chain on FP32 CUDA cores (measured
+                             variant and cross-check of the tensor-core chain)          */
 
 /* weight update */
 #define FTQ_PHASELESS 0   /* w <- |I_k| max(0, cos theta_k)  (Eqs. import, phimport, theta) */
@@ -55,7 +58,7 @@ typedef struct {
     int      walkers;          /* W > 0                                                  */
     int      stabilise_every;  /* s: QRCP of the right block every s slices (0 = never)   */
     int      exp_order;        /* p >= 1: Taylor order of exp(V)                          */
-    int      precision;        /* FTQ_FP64 or FTQ_MIXED                                   */
+    int      precision;        /* FTQ_FP64, FTQ_MIXED or FTQ_MIXED_SIMT                   */
     int      constraint;       /* FTQ_PHASELESS or FTQ_FREE                               */
     int      reserved;         /* must be 0                                               */
     uint64_t seed;             /* reserved for the on-device field generator              */
@@ -117,8 +120,10 @@ int ftq_estimators(ftq_ctx* ctx, double* out_host, double* per_walker_dev);
  * last slice (Eq. import). */
 int ftq_weights(ftq_ctx* ctx, double* out_dev);
 
-/* Read and clear the latched device status (FTQ_OK or FTQ_ENUMERIC);
- * synchronises the stream. */
+/* Read and clear the latched device status: FTQ_OK, FTQ_ENUMERIC (zero or
+ * NaN pivot, non-finite log-determinant) or FTQ_ETIMEOUT (a tensor-core
+ * kernel gave up a bounded wait on its own copies and left its output
+ * unwritten); synchronises the stream. */
 int ftq_status(ftq_ctx* ctx, int* status_host);
 
 /* Integer properties. */

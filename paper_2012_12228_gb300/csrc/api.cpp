@@ -62,7 +62,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     if (opts->walkers <= 0) return fail(nullptr, FTQ_EINVAL, "walkers must be positive");
     if (opts->exp_order < 1 || opts->exp_order > 32) return fail(nullptr, FTQ_EINVAL, "exp_order must be in 1..32");
     if (opts->stabilise_every < 0) return fail(nullptr, FTQ_EINVAL, "stabilise_every must be >= 0");
-    if (opts->precision != FTQ_FP64 && opts->precision != FTQ_MIXED)
+    if (opts->precision != FTQ_FP64 && opts->precision != FTQ_MIXED && opts->precision != FTQ_MIXED_SIMT)
         return fail(nullptr, FTQ_EINVAL, "unknown precision");
     if (opts->constraint != FTQ_PHASELESS && opts->constraint != FTQ_FREE)
         return fail(nullptr, FTQ_EINVAL, "unknown constraint");
@@ -90,9 +90,9 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     if (opts->precision == FTQ_FP64) {
         chk(dalloc(c, &c->Y, W * MM));
     } else {
-        c->Kp = (M + 7) / 8 * 8;
+        c->Kp = (M + 15) / 16 * 16;       // 2 Kp is a whole number of 32-float k tiles
         c->LD = (M + 7) / 8 * 8;
-        const size_t wsz = 4 * (size_t)c->Kp * c->LD;
+        const size_t wsz = 2 * (size_t)c->LD * 2 * c->Kp;
         chk(dalloc(c, &c->Ypl, W * wsz));
         chk(dalloc(c, &c->zpl[0], W * wsz));
         chk(dalloc(c, &c->zpl[1], W * wsz));
@@ -133,6 +133,14 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         chk(upload(c, &c->tab.vq, s.vq));
         chk(upload(c, &c->tab.ksq, ksq));
         chk(upload(c, &c->tab.g0, g0));
+    }
+    if (e == cudaSuccess && opts->precision == FTQ_MIXED) {
+        if (!ftq::tc_supported(M)) {
+            free_all(c);
+            delete c;
+            return fail(nullptr, FTQ_ECUDA, "the driver does not expose cuTensorMapEncodeTiled");
+        }
+        chk(ftq::tc_make_maps(c));
     }
     if (e == cudaSuccess) chk(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     if (e == cudaSuccess) chk(ftq::launch_init_walkers(c));
@@ -215,7 +223,7 @@ int ftq_status(ftq_ctx* c, int* status_host) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "status");
-    *status_host = v ? FTQ_ENUMERIC : FTQ_OK;
+    *status_host = (v & 2) ? FTQ_ETIMEOUT : (v ? FTQ_ENUMERIC : FTQ_OK);
     return FTQ_OK;
 }
 

@@ -1,0 +1,455 @@
+// One Taylor-Horner step of exp(V) on the mixed-precision chain with the
+// 5th-generation tensor cores: tcgen05.mma kind::tf32, 3xTF32 splitting
+// (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM), B operand streamed by
+// TMA, A operand generated in shared memory from the walker's field table.
+//
+// Complex product as one real GEMM.  For 64 complex rows of the output the
+// MMA rows are [Re C (64) ; Im C (64)] and the contraction index runs over
+// [Re Z (Kp) ; Im Z (Kp)]:
+//   Re C = Vr Zr - Vi Zi,   Im C = Vi Zr + Vr Zi,
+// so the 128 x 2Kp A tile is [[Vr, -Vi], [Vi, Vr]] (rows of this walker's
+// V gathered from phi) and the B tile is the chain stored K-major (row c =
+// column c of Z as [Re | Im]), i.e. exactly the layout of the chain planes.
+//
+// One CTA = one walker x one block of 64 complex rows x all N columns (N <=
+// 256).  Two shared-memory stages: while the tensor core runs k tile t the
+// threads generate the A tile of t+1 and TMA fetches its B tile.  Every
+// mbarrier wait is bounded; on expiry the kernel sets bit 2 of the status
+// word, drains its own copies and MMAs (bounded) and frees TMEM.
+//
+// Outputs the rows/columns covered by the MMA tile; k_chain_border handles
+// the rest (for M = 257: row 256 and column 256).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+
+#include "complex_math.cuh"
+#include "ftq_internal.h"
+#include "mixed_common.cuh"
+
+namespace ftq {
+namespace {
+
+constexpr int KTILE = 32;            // floats per k tile = 128 bytes = one swizzle row
+constexpr int AROWS = 128;           // MMA M
+constexpr int NTHREADS = 256;
+constexpr long WAIT_LIMIT = 1L << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on one phase of an mbarrier.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D(tmem) (+)= A(smem) * B(smem)^T, both K-major, issued by one thread.
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // version
+    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(AROWS >> 4) << 24);
+}
+
+// Element (r, k) of a 128 x 32 K-major tile in the 128-byte swizzled layout.
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
+}
+
+struct TcArgs {
+    const float* Yu;
+    float* out;
+    const double2* phi;
+    const uint16_t* vidx;
+    const double* zs;
+    const double* us;
+    const double* os;
+    float alpha;
+    int M, nslot, Kp, LDc, NT, ktiles, ncols;
+    int* status;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant__ CUtensorMap zmap, TcArgs p) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t tma_bar[2], mma_bar[2];
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rb = blockIdx.x, w = blockIdx.y;
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    unsigned char* base = smem_raw + pad;
+    const uint32_t a_bytes = AROWS * KTILE * 4;
+    const uint32_t b_bytes = (uint32_t)p.NT * KTILE * 4;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    float2* phs = reinterpret_cast<float2*>(base + 2 * stage_bytes);
+
+    if (tid == 0) {
+        mbar_init(&tma_bar[0], 1);
+        mbar_init(&tma_bar[1], 1);
+        mbar_init(&mma_bar[0], 1);
+        mbar_init(&mma_bar[1], 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&tmem_sh, (uint32_t)p.ncols);
+    const double2* ph = p.phi + (long)w * p.nslot;
+    for (int i = tid; i < p.nslot; i += NTHREADS) {
+        double2 d = ph[i];
+        phs[i] = make_float2((float)d.x, (float)d.y);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+    const uint32_t idesc = idesc_tf32(p.NT);
+    const int rows0 = rb * 64;
+    int last_tma = -1, last_mma = -1;   // meaningful in thread 0
+    bool bad = false;
+
+    for (int kt = 0; kt < p.ktiles; ++kt) {
+        const int s = kt & 1, use = kt >> 1;
+        if (kt >= 2) {
+            bool ok = mbar_wait(&mma_bar[s], (uint32_t)((use - 1) & 1));
+            if (__syncthreads_or(!ok)) { bad = true; break; }
+        }
+        unsigned char* Ahi = base + s * stage_bytes;
+        unsigned char* Alo = Ahi + a_bytes;
+        unsigned char* Bhi = Alo + a_bytes;
+        unsigned char* Blo = Bhi + b_bytes;
+        if (tid == 0) {
+            mbar_expect_tx(&tma_bar[s], 2 * b_bytes);
+            tma_load_2d(Bhi, &zmap, kt * KTILE, (2 * w) * p.LDc, &tma_bar[s]);
+            tma_load_2d(Blo, &zmap, kt * KTILE, (2 * w + 1) * p.LDc, &tma_bar[s]);
+            last_tma = kt;
+        }
+        // A tile: row j (Re C) and row 64 + j (Im C) for complex row rows0 + j
+        const int kk = lane;
+        const int kg = kt * KTILE + kk;
+        const bool im_half = kg >= p.Kp;
+        const int kc = im_half ? kg - p.Kp : kg;
+        const float zsc = (p.zs != nullptr && kc < p.M) ? (float)p.zs[kc] : 1.0f;
+        for (int j = warp; j < 64; j += NTHREADS / 32) {
+            const int i = rows0 + j;
+            float2 v = make_float2(0.f, 0.f);
+            if (i < p.M && kc < p.M) {
+                v = phs[p.vidx[(long)i * p.M + kc]];
+                v.x *= zsc;
+                v.y *= zsc;
+            }
+            const float top = im_half ? -v.y : v.x;
+            const float bot = im_half ? v.x : v.y;
+            float h, l;
+            split_tf32(top, h, l);
+            uint32_t o = sw128_offset(j, kk);
+            *reinterpret_cast<float*>(Ahi + o) = h;
+            *reinterpret_cast<float*>(Alo + o) = l;
+            split_tf32(bot, h, l);
+            o = sw128_offset(64 + j, kk);
+            *reinterpret_cast<float*>(Ahi + o) = h;
+            *reinterpret_cast<float*>(Alo + o) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (!mbar_wait(&tma_bar[s], (uint32_t)(use & 1))) {
+                atomicOr(p.status, 2);
+                abort_sh = 1;
+            } else {
+                tc_fence_after();
+                const uint64_t ah = sdesc_sw128(Ahi), al = sdesc_sw128(Alo);
+                const uint64_t bh = sdesc_sw128(Bhi), bl = sdesc_sw128(Blo);
+#pragma unroll
+                for (int k = 0; k < KTILE / 8; ++k) {
+                    const uint64_t dk = (uint64_t)((k * 32) >> 4);   // 8 tf32 = 32 bytes along the row
+                    mma_tf32(tmem, ah + dk, bh + dk, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                    mma_tf32(tmem, ah + dk, bl + dk, idesc, 1u);
+                    mma_tf32(tmem, al + dk, bh + dk, idesc, 1u);
+                }
+                mma_commit(&mma_bar[s]);
+                last_mma = kt;
+            }
+        }
+        __syncthreads();
+        if (abort_sh) { bad = true; break; }
+    }
+    if (!bad) {
+        const int last = p.ktiles - 1;
+        bool ok = mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1));
+        if (__syncthreads_or(!ok)) bad = true;
+    }
+    tc_fence_after();
+    if (!bad) {
+        const int r = (warp & 3) * 32 + lane;        // accumulator row = TMEM lane
+        const int i = rows0 + (r & 63);
+        const int part = r >> 6;                      // 0: Re C, 1: Im C
+        const bool row_ok = i < p.M;
+        const float usi = row_ok ? (float)p.us[i] : 0.f;
+        const float osi = (row_ok && p.os != nullptr) ? (float)p.os[i] : 1.f;
+        const size_t rowlen = 2 * (size_t)p.Kp;
+        const size_t partoff = (size_t)p.LDc * rowlen;
+        const size_t wstride = 2 * partoff;
+        const float* U = p.Yu + wstride * w;
+        float* O = p.out + wstride * w;
+        const int ncol = p.NT < p.M ? p.NT : p.M;
+        for (int ch = warp >> 2; ch * 16 < p.NT; ch += 2) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ch * 16), v);
+            if (row_ok) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = ch * 16 + q;
+                    if (c < ncol) {
+                        const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
+                        const float u = U[o] + U[partoff + o];
+                        const float val = osi * (usi * u + p.alpha * __uint_as_float(v[q]));
+                        float h, l;
+                        split_tf32(val, h, l);
+                        O[o] = h;
+                        O[partoff + o] = l;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (bad && tid == 0) {
+        atomicOr(p.status, 2);
+        if (last_tma >= 0) mbar_wait(&tma_bar[last_tma & 1], (uint32_t)((last_tma >> 1) & 1));
+        if (last_mma >= 0) mbar_wait(&mma_bar[last_mma & 1], (uint32_t)((last_mma >> 1) & 1));
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)p.ncols);
+}
+
+// Output entries outside the MMA tile: rows [R, M) x all columns and
+// columns [NT, M) x rows [0, R), on CUDA cores in FP32 from the same
+// hi + lo operands.
+__global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ Zin, const float* __restrict__ Yu,
+                                                     float* __restrict__ out, const double2* __restrict__ phi,
+                                                     const uint16_t* __restrict__ vidx,
+                                                     const double* __restrict__ zs, const double* __restrict__ us,
+                                                     const double* __restrict__ os, float alpha, int M, int nslot,
+                                                     Planes P, size_t wstride, int R, int NT) {
+    const int w = blockIdx.x;
+    const float* Z = Zin + wstride * w;
+    const float* U = Yu + wstride * w;
+    float* O = out + wstride * w;
+    const double2* ph = phi + (long)w * nslot;
+    const int Rr = R < M ? R : M;               // rows produced by the MMA tile
+    const int nrow = M - Rr;                    // border rows
+    const int ncolb = M > NT ? M - NT : 0;      // border columns
+    const long total = (long)nrow * M + (long)ncolb * Rr;
+    for (long e = threadIdx.x; e < total; e += blockDim.x) {
+        int i, c;
+        if (e < (long)nrow * M) {
+            i = Rr + (int)(e / M);
+            c = (int)(e % M);
+        } else {
+            long e2 = e - (long)nrow * M;
+            c = NT + (int)(e2 / Rr);
+            i = (int)(e2 % Rr);
+        }
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k = 0; k < M; ++k) {
+            double2 d = ph[vidx[(long)i * M + k]];
+            float sk = zs ? (float)zs[k] : 1.0f;
+            float2 v = make_float2((float)d.x * sk, (float)d.y * sk);
+            acc = cfma(v, P.load(Z, k, c), acc);
+        }
+        float2 u = P.load(U, i, c);
+        float s = (float)us[i];
+        float2 val = make_float2(u.x * s + alpha * acc.x, u.y * s + alpha * acc.y);
+        if (os) {
+            float o = (float)os[i];
+            val.x *= o;
+            val.y *= o;
+        }
+        P.store(O, i, c, val);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+}  // namespace
+
+// Tile plan for basis size M: rows covered by 64-row MMA blocks (R, possibly
+// padded above M) and the MMA N width (<= 256).
+void tc_plan(int M, int* R, int* NT) {
+    int rem = M % 64;
+    if (rem == 0) *R = M;
+    else if (M > 64 && rem <= 8) *R = M - rem;          // a thin border row band on CUDA cores
+    else *R = (M + 63) / 64 * 64;                       // padded rows, not stored
+    *NT = M <= 256 ? (M + 15) / 16 * 16 : 256;
+}
+
+bool tc_supported(int M) {
+    (void)M;
+    return encode_fn() != nullptr;
+}
+
+// One tensor map per chain buffer: [W * 2 * LDc rows] x [2 Kp floats],
+// boxes of 32 floats x NT rows, 128-byte swizzle.
+cudaError_t tc_make_maps(ftq_ctx* c) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    int R, NT;
+    tc_plan(c->M, &R, &NT);
+    float* bufs[3] = {c->Ypl, c->zpl[0], c->zpl[1]};
+    for (int b = 0; b < 3; ++b) {
+        cuuint64_t dims[2] = {(cuuint64_t)(2 * c->Kp), (cuuint64_t)c->W * 2 * c->LD};
+        cuuint64_t strides[1] = {(cuuint64_t)(2 * c->Kp) * sizeof(float)};
+        cuuint32_t box[2] = {(cuuint32_t)KTILE, (cuuint32_t)NT};
+        cuuint32_t estr[2] = {1, 1};
+        CUtensorMap* m = reinterpret_cast<CUtensorMap*>(c->tmap[b]);
+        CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, bufs[b], dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        c->tmap_buf[b] = bufs[b];
+    }
+    return cudaSuccess;
+}
+
+cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double* zs, const double* os,
+                          float alpha) {
+    const CUtensorMap* map = nullptr;
+    for (int b = 0; b < 3; ++b)
+        if (c->tmap_buf[b] == zin) map = reinterpret_cast<const CUtensorMap*>(c->tmap[b]);
+    if (!map) return cudaErrorInvalidValue;
+    int R, NT;
+    tc_plan(c->M, &R, &NT);
+    TcArgs a;
+    a.Yu = c->Ypl;
+    a.out = out;
+    a.phi = c->phi;
+    a.vidx = c->tab.vidx;
+    a.zs = zs;
+    a.us = c->tab.h;
+    a.os = os;
+    a.alpha = alpha;
+    a.M = c->M;
+    a.nslot = c->nslot;
+    a.Kp = c->Kp;
+    a.LDc = c->LD;
+    a.NT = NT;
+    a.ktiles = 2 * c->Kp / KTILE;
+    a.ncols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    a.status = c->status;
+    const size_t stage = 2 * (size_t)AROWS * KTILE * 4 + 2 * (size_t)NT * KTILE * 4;
+    const size_t smem = 1024 + 2 * stage + sizeof(float2) * c->nslot;
+    cudaError_t e = cudaFuncSetAttribute(k_chain_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls(c, FTQ_K_CHAIN);
+        k_chain_tc<<<dim3((unsigned)(R / 64), (unsigned)c->W), NTHREADS, smem, c->stream>>>(*map, a);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (R < c->M || NT < c->M) {
+        Planes P;
+        P.Kp = c->Kp;
+        P.part = (size_t)c->LD * 2 * c->Kp;
+        LaunchScope ls(c, FTQ_K_CHAIN);
+        k_chain_border<<<c->W, 256, 0, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, zs, c->tab.h, os, alpha,
+                                                   c->M, c->nslot, P, 2 * P.part, R, NT);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace ftq

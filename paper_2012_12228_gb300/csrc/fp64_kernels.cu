@@ -563,7 +563,7 @@ cudaError_t launch_init_walkers(ftq_ctx* c) {
     c->k = 0;
     c->g64_valid = true;
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && c->opts.precision == FTQ_MIXED) e = mixed_init(c);
+    if (e == cudaSuccess && c->opts.precision != FTQ_FP64) e = mixed_init(c);
     return e;
 }
 
@@ -581,12 +581,12 @@ cudaError_t launch_force_bias_any(ftq_ctx* c, const double* x, const void* G, bo
 }
 
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x) {
-    if (c->opts.precision == FTQ_MIXED && c->k > 0) return launch_force_bias_any(c, x, c->G32, true);
+    if (c->opts.precision != FTQ_FP64 && c->k > 0) return launch_force_bias_any(c, x, c->G32, true);
     return launch_force_bias_any(c, x, c->G, false);
 }
 
 cudaError_t launch_chain(ftq_ctx* c) {
-    if (c->opts.precision == FTQ_MIXED) return mixed_chain(c);
+    if (c->opts.precision != FTQ_FP64) return mixed_chain(c);
     const int M = c->M, p = c->opts.exp_order;
     const int tiles = (M + CT - 1) / CT;
     dim3 grid(tiles * tiles, c->W);
@@ -620,7 +620,7 @@ cudaError_t launch_qrcp64(ftq_ctx* c, const double2* Yin, double2* Qout) {
 }
 
 cudaError_t launch_qrcp(ftq_ctx* c) {
-    if (c->opts.precision == FTQ_MIXED) return mixed_qrcp(c);
+    if (c->opts.precision != FTQ_FP64) return mixed_qrcp(c);
     cudaError_t e = launch_qrcp64(c, c->Y, c->zbuf[0]);
     double2* q = c->zbuf[0];
     c->zbuf[0] = c->Y;
@@ -641,7 +641,7 @@ cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update) {
 }
 
 cudaError_t launch_green(ftq_ctx* c, int k, bool update) {
-    if (c->opts.precision == FTQ_MIXED) return mixed_green(c, k);
+    if (c->opts.precision != FTQ_FP64) return mixed_green(c, k);
     return launch_green64(c, c->Y, k, update);
 }
 

@@ -73,6 +73,9 @@ struct ftq_ctx {
     float2* w32 = nullptr;        // FP32 LU workspace                        [W][M][M]
     float2* w2_32 = nullptr;      // FP32 solve workspace                     [W][M][M]
     bool g64_valid = true;        // G holds the current G(tau) (mixed: only at k = 0, n)
+    // TMA descriptors (CUtensorMap, 128 bytes) of the three chain buffers
+    alignas(64) unsigned char tmap[3][128] = {};
+    const float* tmap_buf[3] = {nullptr, nullptr, nullptr};
     double2* DR = nullptr;        // D_R                                       [W][M]
     double2* phi = nullptr;       // V generator table per walker              [W][nslot]
     double2* hh = nullptr;        // Householder u_0 per column                [W][M]
@@ -148,5 +151,12 @@ cudaError_t mixed_chain(ftq_ctx* c);
 cudaError_t mixed_qrcp(ftq_ctx* c);
 cudaError_t mixed_green(ftq_ctx* c, int k);
 cudaError_t mixed_sync_g64(ftq_ctx* c);    // make G (complex128) hold G(tau) now
+
+// Tensor-core chain (chain_tc.cu).
+void tc_plan(int M, int* R, int* NT);
+bool tc_supported(int M);
+cudaError_t tc_make_maps(ftq_ctx* c);
+cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double* zs, const double* os,
+                          float alpha);
 
 }  // namespace ftq

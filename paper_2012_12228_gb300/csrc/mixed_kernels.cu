@@ -7,42 +7,12 @@
 
 #include "complex_math.cuh"
 #include "ftq_internal.h"
+#include "mixed_common.cuh"
 
 namespace ftq {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-
-__device__ __forceinline__ float tf32_rna(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
-}
-
-// v ~= hi + lo with hi, lo both tf32 values (|v - hi - lo| <= 2^-22 |v|)
-__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
-    hi = tf32_rna(v);
-    lo = tf32_rna(v - hi);
-}
-
-struct Planes {
-    size_t plane;    // Kp * LD
-    int LD;
-    __device__ __forceinline__ float2 load(const float* w, int i, int c) const {
-        size_t o = (size_t)i * LD + c;
-        return make_float2(w[o] + w[2 * plane + o], w[plane + o] + w[3 * plane + o]);
-    }
-    __device__ __forceinline__ void store(float* w, int i, int c, float2 v) const {
-        size_t o = (size_t)i * LD + c;
-        float h, l;
-        split_tf32(v.x, h, l);
-        w[o] = h;
-        w[2 * plane + o] = l;
-        split_tf32(v.y, h, l);
-        w[plane + o] = h;
-        w[3 * plane + o] = l;
-    }
-};
 
 template <typename T>
 __device__ T block_sum(T v, T* sh) {
@@ -86,42 +56,42 @@ __device__ int block_argmax(float val, int idx, float* shv, int* shi) {
 }
 
 // ---------------------------------------------------------------- layout bridges
-__global__ void k_planes_identity(float* Ypl, size_t plane, int LD, int M, size_t wstride, int W) {
+__global__ void k_planes_identity(float* Ypl, int Kp, int M, size_t wstride, int W) {
     long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (e >= (long)W * M) return;
     int w = (int)(e / M), i = (int)(e % M);
-    Ypl[wstride * w + (size_t)i * LD + i] = 1.0f;
+    Ypl[wstride * w + (size_t)i * (2 * Kp) + i] = 1.0f;
 }
 
-__global__ void k_planes_to_c128(const float* __restrict__ Ypl, double2* __restrict__ Y, size_t plane, int LD,
-                                 int M, size_t wstride, long total) {
+__global__ void k_planes_to_c128(const float* __restrict__ Ypl, double2* __restrict__ Y, Planes P, int M,
+                                 size_t wstride, long total) {
     long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (e >= total) return;
     long w = e / ((long)M * M);
     int ij = (int)(e % ((long)M * M));
     int i = ij / M, c = ij % M;
     const float* p = Ypl + wstride * w;
-    size_t o = (size_t)i * LD + c;
-    Y[e] = make_double2((double)p[o] + (double)p[2 * plane + o], (double)p[plane + o] + (double)p[3 * plane + o]);
+    size_t o = (size_t)c * (2 * P.Kp) + i;
+    Y[e] = make_double2((double)p[o] + (double)p[P.part + o], (double)p[o + P.Kp] + (double)p[P.part + o + P.Kp]);
 }
 
-__global__ void k_c128_to_planes(const double2* __restrict__ Y, float* __restrict__ Ypl, size_t plane, int LD,
-                                 int M, size_t wstride, long total) {
+__global__ void k_c128_to_planes(const double2* __restrict__ Y, float* __restrict__ Ypl, Planes P, int M,
+                                 size_t wstride, long total) {
     long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (e >= total) return;
     long w = e / ((long)M * M);
     int ij = (int)(e % ((long)M * M));
     int i = ij / M, c = ij % M;
     float* p = Ypl + wstride * w;
-    size_t o = (size_t)i * LD + c;
+    size_t o = (size_t)c * (2 * P.Kp) + i;
     double2 v = Y[e];
     // hi = tf32(v), lo = tf32(v - hi) computed in double so the pair keeps ~22 bits
     float h = tf32_rna((float)v.x);
     p[o] = h;
-    p[2 * plane + o] = tf32_rna((float)(v.x - (double)h));
+    p[P.part + o] = tf32_rna((float)(v.x - (double)h));
     h = tf32_rna((float)v.y);
-    p[plane + o] = h;
-    p[3 * plane + o] = tf32_rna((float)(v.y - (double)h));
+    p[o + P.Kp] = h;
+    p[P.part + o + P.Kp] = tf32_rna((float)(v.y - (double)h));
 }
 
 __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict__ b, long total) {
@@ -358,12 +328,12 @@ int fact_threads(int M) {
 
 Planes planes_of(const ftq_ctx* c) {
     Planes P;
-    P.plane = (size_t)c->Kp * c->LD;
-    P.LD = c->LD;
+    P.Kp = c->Kp;
+    P.part = (size_t)c->LD * 2 * c->Kp;
     return P;
 }
 
-size_t walker_stride(const ftq_ctx* c) { return 4 * (size_t)c->Kp * c->LD; }
+size_t walker_stride(const ftq_ctx* c) { return 2 * (size_t)c->LD * 2 * c->Kp; }
 
 }  // namespace
 
@@ -376,8 +346,7 @@ cudaError_t mixed_init(ftq_ctx* c) {
     {
         LaunchScope ls(c, FTQ_K_INIT);
         long n = (long)W * M;
-        k_planes_identity<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->Ypl, (size_t)c->Kp * c->LD, c->LD,
-                                                                             M, ws, W);
+        k_planes_identity<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->Ypl, c->Kp, M, ws, W);
     }
     {
         LaunchScope ls(c, FTQ_K_INIT);
@@ -390,6 +359,7 @@ cudaError_t mixed_init(ftq_ctx* c) {
 
 cudaError_t mixed_chain(ftq_ctx* c) {
     const int M = c->M, p = c->opts.exp_order;
+    const bool tensor = c->opts.precision == FTQ_MIXED;
     const int tiles = (M + ST - 1) / ST;
     dim3 grid(tiles * tiles, c->W);
     const Planes P = planes_of(c);
@@ -398,10 +368,16 @@ cudaError_t mixed_chain(ftq_ctx* c) {
     int cur = 0;
     for (int j = p; j >= 1; --j) {
         float* out = c->zpl[cur];
-        LaunchScope ls(c, FTQ_K_CHAIN);
-        k_chain32<<<grid, 256, 0, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, j == p ? c->tab.h : nullptr,
-                                               c->tab.h, j == 1 ? c->tab.h : nullptr, 1.0f / j, M, c->nslot, tiles,
-                                               P, ws);
+        const double* zs = j == p ? c->tab.h : nullptr;
+        const double* os = j == 1 ? c->tab.h : nullptr;
+        if (tensor) {
+            cudaError_t e = tc_chain_step(c, zin, out, zs, os, 1.0f / j);
+            if (e != cudaSuccess) return e;
+        } else {
+            LaunchScope ls(c, FTQ_K_CHAIN);
+            k_chain32<<<grid, 256, 0, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, zs, c->tab.h, os,
+                                                   1.0f / j, M, c->nslot, tiles, P, ws);
+        }
         zin = out;
         cur ^= 1;
     }
@@ -415,17 +391,18 @@ cudaError_t mixed_qrcp(ftq_ctx* c) {
     const int M = c->M;
     const long n = (long)c->W * M * M;
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    const size_t ws = walker_stride(c), plane = (size_t)c->Kp * c->LD;
+    const size_t ws = walker_stride(c);
+    const Planes P = planes_of(c);
     double2* y64 = c->zbuf[1];
     double2* q64 = c->zbuf[0];
     {
         LaunchScope ls(c, FTQ_K_QRCP);
-        k_planes_to_c128<<<blocks, 256, 0, c->stream>>>(c->Ypl, y64, plane, c->LD, M, ws, n);
+        k_planes_to_c128<<<blocks, 256, 0, c->stream>>>(c->Ypl, y64, P, M, ws, n);
     }
     cudaError_t e = launch_qrcp64(c, y64, q64);
     if (e != cudaSuccess) return e;
     LaunchScope ls(c, FTQ_K_QRCP);
-    k_c128_to_planes<<<blocks, 256, 0, c->stream>>>(q64, c->Ypl, plane, c->LD, M, ws, n);
+    k_c128_to_planes<<<blocks, 256, 0, c->stream>>>(q64, c->Ypl, P, M, ws, n);
     return cudaGetLastError();
 }
 
@@ -437,7 +414,7 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
         {
             LaunchScope ls(c, FTQ_K_GREEN);
             k_planes_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-                c->Ypl, c->zbuf[1], (size_t)c->Kp * c->LD, c->LD, M, walker_stride(c), n);
+                c->Ypl, c->zbuf[1], planes_of(c), M, walker_stride(c), n);
         }
         cudaError_t e = launch_green64(c, c->zbuf[1], k, true);
         c->g64_valid = true;

@@ -39,12 +39,37 @@ def weighted_e_per_electron(est, N):
     return est["E"].real / N
 
 
-def test_mixed_vs_oracle_config1(ftq):
+@pytest.mark.parametrize("wl,W,n", [("ueg_n2_m7", 16, 3), ("ueg_n14_m57", 8, 6), ("ueg_n14_m123", 4, 6),
+                                    ("ueg_n66_m257", 4, 6)])
+def test_tensor_chain_matches_cuda_core_chain(ftq, wl, W, n):
+    """tcgen05 3xTF32 chain vs the FP32 CUDA-core chain on the same fields:
+    both hold the chain to ~2^-22; they differ by the dropped lo*lo product
+    and the summation order, so G agrees to ~1e-6 after a QRCP block."""
+    c = WORKLOADS[wl]
+    f = torch.from_numpy(gaussian_fields(c["seed"], n, W, UEG(c["N"], c["M"], c["rs"], c["theta"],
+                                                               c["dtau"]).N_alpha)).cuda()
+    out = {}
+    for prec in (ftq.FTQ_MIXED_SIMT, ftq.FTQ_MIXED):
+        p = make(ftq, wl, W, prec)
+        p.propagate(f)
+        out[prec] = (p.green().cpu().numpy(), p.weights().cpu().numpy())
+        assert p.status() == 0
+        p.close()
+    ga, gb = out[ftq.FTQ_MIXED_SIMT][0], out[ftq.FTQ_MIXED][0]
+    err = np.abs(ga - gb).max() / np.abs(ga).max()
+    lerr = np.abs(out[ftq.FTQ_MIXED_SIMT][1][:, 3] - out[ftq.FTQ_MIXED][1][:, 3]).max()
+    print(f"{wl}: tensor vs CUDA-core chain, G rel err {err:.2e}, ln det abs err {lerr:.2e}")
+    assert err < 1e-5
+    assert lerr < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["mixed", "mixed_simt"])
+def test_mixed_vs_oracle_config1(ftq, prec):
     c = WORKLOADS["ueg_n2_m7"]
     s = UEG(c["N"], c["M"], c["rs"], c["theta"], c["dtau"])
     W = 32
     f = gaussian_fields(c["seed"], s.n_slices, W, s.N_alpha)
-    p = make(ftq, "ueg_n2_m7", W, ftq.FTQ_MIXED)
+    p = make(ftq, "ueg_n2_m7", W, ftq.FTQ_MIXED if prec == "mixed" else ftq.FTQ_MIXED_SIMT)
     fd = torch.from_numpy(f).cuda()
     p.propagate(fd[:10].contiguous())
     G10 = p.green().cpu().numpy()
