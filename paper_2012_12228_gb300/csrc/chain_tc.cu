@@ -209,14 +209,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
         const int kg = kt * KTILE + kk;
         const bool im_half = kg >= p.Kp;
         const int kc = im_half ? kg - p.Kp : kg;
-        const float zsc = (p.zs != nullptr && kc < p.M) ? (float)p.zs[kc] : 1.0f;
+        const ScaleF zsc((p.zs != nullptr && kc < p.M) ? p.zs[kc] : 1.0);
         for (int j = warp; j < 64; j += NTHREADS / 32) {
             const int i = rows0 + j;
             float2 v = make_float2(0.f, 0.f);
             if (i < p.M && kc < p.M) {
                 v = phs[p.vidx[(long)i * p.M + kc]];
-                v.x *= zsc;
-                v.y *= zsc;
+                v.x = zsc(v.x);
+                v.y = zsc(v.y);
             }
             const float top = im_half ? -v.y : v.x;
             const float bot = im_half ? v.x : v.y;
@@ -265,8 +265,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
         const int i = rows0 + (r & 63);
         const int part = r >> 6;                      // 0: Re C, 1: Im C
         const bool row_ok = i < p.M;
-        const float usi = row_ok ? (float)p.us[i] : 0.f;
-        const float osi = (row_ok && p.os != nullptr) ? (float)p.os[i] : 1.f;
+        const ScaleF usi(row_ok ? p.us[i] : 0.0);
+        const ScaleF osi((row_ok && p.os != nullptr) ? p.os[i] : 1.0);
         const size_t rowlen = 2 * (size_t)p.Kp;
         const size_t partoff = (size_t)p.LDc * rowlen;
         const size_t wstride = 2 * partoff;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
                     if (c < ncol) {
                         const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
                         const float u = U[o] + U[partoff + o];
-                        const float val = osi * (usi * u + p.alpha * __uint_as_float(v[q]));
+                        const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(u)));
                         float h, l;
                         split_tf32(val, h, l);
                         O[o] = h;
@@ -336,17 +336,17 @@ __global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ 
         float2 acc = make_float2(0.f, 0.f);
         for (int k = 0; k < M; ++k) {
             double2 d = ph[vidx[(long)i * M + k]];
-            float sk = zs ? (float)zs[k] : 1.0f;
-            float2 v = make_float2((float)d.x * sk, (float)d.y * sk);
+            const ScaleF sk(zs ? zs[k] : 1.0);
+            float2 v = make_float2(sk((float)d.x), sk((float)d.y));
             acc = cfma(v, P.load(Z, k, c), acc);
         }
         float2 u = P.load(U, i, c);
-        float s = (float)us[i];
-        float2 val = make_float2(u.x * s + alpha * acc.x, u.y * s + alpha * acc.y);
+        const ScaleF s(us[i]);
+        float2 val = make_float2(fmaf(alpha, acc.x, s(u.x)), fmaf(alpha, acc.y, s(u.y)));
         if (os) {
-            float o = (float)os[i];
-            val.x *= o;
-            val.y *= o;
+            const ScaleF o(os[i]);
+            val.x = o(val.x);
+            val.y = o(val.y);
         }
         P.store(O, i, c, val);
     }

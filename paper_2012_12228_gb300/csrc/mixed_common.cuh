@@ -18,6 +18,19 @@ __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
     lo = tf32_rna(v - hi);
 }
 
+// x * s for a scale s held in double: s is split into a float pair
+// (hi + lo) so that the product carries no systematic rounding of s.  The
+// kinetic factors multiply the chain on every slice; a float-rounded factor
+// would bias ln D by n times its rounding error over a path of n slices.
+struct ScaleF {
+    float hi, lo;
+    __device__ __forceinline__ explicit ScaleF(double s) {
+        hi = (float)s;
+        lo = (float)(s - (double)hi);
+    }
+    __device__ __forceinline__ float operator()(float x) const { return fmaf(lo, x, hi * x); }
+};
+
 // Chain layout (mixed): per walker two parts (tf32 hi, tf32 lo), each LDc
 // rows of 2 Kp floats; row c holds column c of Y as [Re Y[0..Kp) | Im Y[0..Kp)].
 // A row is one K-major operand row of the real-embedded product, so the

@@ -173,9 +173,13 @@ __global__ void __launch_bounds__(256) k_chain32(const float* __restrict__ Zin, 
             int i = r0 + ty + 16 * a, c = c0 + tx + 16 * b;
             if (i < M && c < M) {
                 float2 u = P.load(U, i, c);
-                float s = (float)us[i];
-                float2 v = make_float2(u.x * s + alpha * acc[a][b].x, u.y * s + alpha * acc[a][b].y);
-                if (os) { float o = (float)os[i]; v.x *= o; v.y *= o; }
+                const ScaleF s(us[i]);
+                float2 v = make_float2(fmaf(alpha, acc[a][b].x, s(u.x)), fmaf(alpha, acc[a][b].y, s(u.y)));
+                if (os) {
+                    const ScaleF o(os[i]);
+                    v.x = o(v.x);
+                    v.y = o(v.y);
+                }
                 P.store(O, i, c, v);
             }
         }
