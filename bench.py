@@ -151,17 +151,28 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def kernel_model(kind, M, W, precision):
-    """(algorithmic real flops of ONE launch, bound, peak TFLOP/s, peak source).
+    """(algorithmic flops of ONE launch, bound, peak TFLOP/s, peak source).
 
-    A complex multiply-add counts 8 real flops."""
+    Real flops; a complex multiply-add counts 8.  The tensor-core chain runs
+    the complex product as three tf32 products (3xTF32), so its tensor work is
+    3 x 8 M^3 per walker and its peak is the tf32 dense rate: the measured
+    bf16 GEMM rate times the nominal tf32/bf16 ratio 1.1/2.25."""
     fp64 = ("alu", FP64_PEAK_TFLOPS, "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz")
     fp32 = ("alu", FP32_PEAK_TFLOPS, "FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz")
+    bf16 = PEAKS.get("bf16_tflops", 1900.0)
+    tf32 = ("tensor", bf16 * 1.1 / 2.25,
+            f"tf32 dense = measured bf16 {bf16:.1f} TFLOP/s x 1.1/2.25 (MEASURED_PEAKS.json)"
+            if "bf16_tflops" in PEAKS else "tf32 dense = fallback bf16 1900 TFLOP/s x 1.1/2.25")
     if kind == "chain":          # one Horner step: V (M x M) times Z (M x M), per walker
+        if precision == "mixed":
+            return (3 * 8.0 * M ** 3 * W,) + tf32
         return (8.0 * M ** 3 * W,) + (fp64 if precision == "fp64" else fp32)
     if kind == "green":          # LU (8/3 M^3) + two triangular solves with M right-hand sides (8 M^3)
         return ((8.0 / 3.0 + 8.0) * M ** 3 * W,) + (fp64 if precision == "fp64" else fp32)
-    if kind == "qrcp":           # Householder QR (16/3) + forming Q (16/3) + T^-1 update (4)
-        return ((16.0 / 3.0 + 16.0 / 3.0 + 4.0) * M ** 3 * W,) + fp64
+    if kind == "qrcp":
+        if precision == "fp64":  # Householder QR (16/3) + forming Q (16/3) + T^-1 update (4)
+            return ((16.0 / 3.0 + 16.0 / 3.0 + 4.0) * M ** 3 * W,) + fp64
+        return ((16.0 / 3.0 + 4.0) * M ** 3 * W,) + fp64     # Q is formed in FP32 (bridge class)
     return None
 
 

@@ -158,6 +158,8 @@ int ftq_transfers(const ftq_ctx* ctx, int32_t* q_host);
 #define FTQ_K_GREEN      3   /* G(tau), ln det(I + A) and the weight update         */
 #define FTQ_K_ESTIMATORS 4   /* per-walker estimators and the walker reduction      */
 #define FTQ_K_INIT       5   /* walker initialisation / reset                      */
+#define FTQ_K_BRIDGE     6   /* layout conversions between the FP32 chain and FP64  */
+#define FTQ_K_BORDER     7   /* chain entries outside the tensor-core tile         */
 #define FTQ_K_COUNT      8
 
 /* Start (enable != 0) or stop per-launch timing.  While on, every kernel

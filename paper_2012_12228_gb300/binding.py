@@ -33,7 +33,8 @@ EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc",
            "ftq_last_error", "ftq_destroy"]
-KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5}
+KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
+           "border": 7}
 K_COUNT = 8
 
 

@@ -307,48 +307,68 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
 
 // Output entries outside the MMA tile: rows [R, M) x all columns and
 // columns [NT, M) x rows [0, R), on CUDA cores in FP32 from the same
-// hi + lo operands.
+// hi + lo operands.  A border row of V (or a border column of Z) is staged in
+// shared memory once and reused for every output of that row (column).
+__device__ __forceinline__ void border_store(float* O, const float* U, const Planes& P, const double* us,
+                                             const double* os, float alpha, int i, int c, float2 acc) {
+    float2 u = P.load(U, i, c);
+    const ScaleF s(us[i]);
+    float2 val = make_float2(fmaf(alpha, acc.x, s(u.x)), fmaf(alpha, acc.y, s(u.y)));
+    if (os) {
+        const ScaleF o(os[i]);
+        val.x = o(val.x);
+        val.y = o(val.y);
+    }
+    P.store(O, i, c, val);
+}
+
 __global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ Zin, const float* __restrict__ Yu,
                                                      float* __restrict__ out, const double2* __restrict__ phi,
                                                      const uint16_t* __restrict__ vidx,
                                                      const double* __restrict__ zs, const double* __restrict__ us,
                                                      const double* __restrict__ os, float alpha, int M, int nslot,
                                                      Planes P, size_t wstride, int R, int NT) {
+    extern __shared__ unsigned char smem_raw[];
+    float2* vec = reinterpret_cast<float2*>(smem_raw);     // [M]: one row of V zs or one column of Z
+    float2* phs = vec + M;                                  // [nslot]
     const int w = blockIdx.x;
     const float* Z = Zin + wstride * w;
     const float* U = Yu + wstride * w;
     float* O = out + wstride * w;
     const double2* ph = phi + (long)w * nslot;
-    const int Rr = R < M ? R : M;               // rows produced by the MMA tile
-    const int nrow = M - Rr;                    // border rows
-    const int ncolb = M > NT ? M - NT : 0;      // border columns
-    const long total = (long)nrow * M + (long)ncolb * Rr;
-    for (long e = threadIdx.x; e < total; e += blockDim.x) {
-        int i, c;
-        if (e < (long)nrow * M) {
-            i = Rr + (int)(e / M);
-            c = (int)(e % M);
-        } else {
-            long e2 = e - (long)nrow * M;
-            c = NT + (int)(e2 / Rr);
-            i = (int)(e2 % Rr);
-        }
-        float2 acc = make_float2(0.f, 0.f);
-        for (int k = 0; k < M; ++k) {
-            double2 d = ph[vidx[(long)i * M + k]];
+    const int Rr = R < M ? R : M;
+    for (int e = threadIdx.x; e < nslot; e += blockDim.x) {
+        const double2 d = ph[e];
+        phs[e] = make_float2((float)d.x, (float)d.y);
+    }
+    __syncthreads();
+    for (int i = Rr; i < M; ++i) {              // border rows: (V zs)[i, :] Z
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
             const ScaleF sk(zs ? zs[k] : 1.0);
-            float2 v = make_float2(sk((float)d.x), sk((float)d.y));
-            acc = cfma(v, P.load(Z, k, c), acc);
+            const float2 v = phs[vidx[(long)i * M + k]];
+            vec[k] = make_float2(sk(v.x), sk(v.y));
         }
-        float2 u = P.load(U, i, c);
-        const ScaleF s(us[i]);
-        float2 val = make_float2(fmaf(alpha, acc.x, s(u.x)), fmaf(alpha, acc.y, s(u.y)));
-        if (os) {
-            const ScaleF o(os[i]);
-            val.x = o(val.x);
-            val.y = o(val.y);
+        __syncthreads();
+        for (int c = threadIdx.x; c < M; c += blockDim.x) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int k = 0; k < M; ++k) acc = cfma(vec[k], P.load(Z, k, c), acc);
+            border_store(O, U, P, us, os, alpha, i, c, acc);
         }
-        P.store(O, i, c, val);
+        __syncthreads();
+    }
+    for (int c = NT; c < M; ++c) {              // border columns: (V zs)[:R, :] Z[:, c]
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            const ScaleF sk(zs ? zs[k] : 1.0);
+            const float2 z = P.load(Z, k, c);
+            vec[k] = make_float2(sk(z.x), sk(z.y));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < Rr; i += blockDim.x) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int k = 0; k < M; ++k) acc = cfma(phs[vidx[(long)i * M + k]], vec[k], acc);
+            border_store(O, U, P, us, os, alpha, i, c, acc);
+        }
+        __syncthreads();
     }
 }
 
@@ -444,8 +464,13 @@ cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double
         Planes P;
         P.Kp = c->Kp;
         P.part = (size_t)c->LD * 2 * c->Kp;
-        LaunchScope ls(c, FTQ_K_CHAIN);
-        k_chain_border<<<c->W, 256, 0, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, zs, c->tab.h, os, alpha,
+        const size_t bsm = sizeof(float2) * (c->M + c->nslot);
+        if (bsm > 48 * 1024) {
+            e = cudaFuncSetAttribute(k_chain_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+            if (e != cudaSuccess) return e;
+        }
+        LaunchScope ls(c, FTQ_K_BORDER);
+        k_chain_border<<<c->W, 256, bsm, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, zs, c->tab.h, os, alpha,
                                                    c->M, c->nslot, P, 2 * P.part, R, NT);
         e = cudaGetLastError();
     }

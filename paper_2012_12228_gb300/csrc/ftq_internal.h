@@ -152,6 +152,14 @@ cudaError_t mixed_qrcp(ftq_ctx* c);
 cudaError_t mixed_green(ftq_ctx* c, int k);
 cudaError_t mixed_sync_g64(ftq_ctx* c);    // make G (complex128) hold G(tau) now
 
+// Blocked FP32 Green's function (green_blocked.cu); used while its shared
+// memory fits.
+size_t green32b_smem(int M);
+cudaError_t launch_green32b(ftq_ctx* c, int k);
+
+// Pre-pivoted stabilisation of the mixed chain (qr_mixed.cu).
+cudaError_t launch_qr_prepiv(ftq_ctx* c);
+
 // Tensor-core chain (chain_tc.cu).
 void tc_plan(int M, int* R, int* NT);
 bool tc_supported(int M);

@@ -75,25 +75,6 @@ __global__ void k_planes_to_c128(const float* __restrict__ Ypl, double2* __restr
     Y[e] = make_double2((double)p[o] + (double)p[P.part + o], (double)p[o + P.Kp] + (double)p[P.part + o + P.Kp]);
 }
 
-__global__ void k_c128_to_planes(const double2* __restrict__ Y, float* __restrict__ Ypl, Planes P, int M,
-                                 size_t wstride, long total) {
-    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    long w = e / ((long)M * M);
-    int ij = (int)(e % ((long)M * M));
-    int i = ij / M, c = ij % M;
-    float* p = Ypl + wstride * w;
-    size_t o = (size_t)c * (2 * P.Kp) + i;
-    double2 v = Y[e];
-    // hi = tf32(v), lo = tf32(v - hi) computed in double so the pair keeps ~22 bits
-    float h = tf32_rna((float)v.x);
-    p[o] = h;
-    p[P.part + o] = tf32_rna((float)(v.x - (double)h));
-    h = tf32_rna((float)v.y);
-    p[o + P.Kp] = h;
-    p[P.part + o + P.Kp] = tf32_rna((float)(v.y - (double)h));
-}
-
 __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict__ b, long total) {
     long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (e >= total) return;
@@ -391,24 +372,7 @@ cudaError_t mixed_chain(ftq_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t mixed_qrcp(ftq_ctx* c) {
-    const int M = c->M;
-    const long n = (long)c->W * M * M;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    const size_t ws = walker_stride(c);
-    const Planes P = planes_of(c);
-    double2* y64 = c->zbuf[1];
-    double2* q64 = c->zbuf[0];
-    {
-        LaunchScope ls(c, FTQ_K_QRCP);
-        k_planes_to_c128<<<blocks, 256, 0, c->stream>>>(c->Ypl, y64, P, M, ws, n);
-    }
-    cudaError_t e = launch_qrcp64(c, y64, q64);
-    if (e != cudaSuccess) return e;
-    LaunchScope ls(c, FTQ_K_QRCP);
-    k_c128_to_planes<<<blocks, 256, 0, c->stream>>>(q64, c->Ypl, P, M, ws, n);
-    return cudaGetLastError();
-}
+cudaError_t mixed_qrcp(ftq_ctx* c) { return launch_qr_prepiv(c); }
 
 cudaError_t mixed_green(ftq_ctx* c, int k) {
     const int M = c->M;
@@ -416,12 +380,17 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
         // tau = beta: the final G and ln det in complex128
         const long n = (long)c->W * M * M;
         {
-            LaunchScope ls(c, FTQ_K_GREEN);
+            LaunchScope ls(c, FTQ_K_BRIDGE);
             k_planes_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
                 c->Ypl, c->zbuf[1], planes_of(c), M, walker_stride(c), n);
         }
         cudaError_t e = launch_green64(c, c->zbuf[1], k, true);
         c->g64_valid = true;
+        return e;
+    }
+    if (green32b_smem(M) <= 220 * 1024) {
+        cudaError_t e = launch_green32b(c, k);
+        c->g64_valid = false;
         return e;
     }
     size_t sm = (2 * sizeof(float2) + 3 * sizeof(float) + sizeof(int)) * M;
@@ -439,7 +408,7 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
 cudaError_t mixed_sync_g64(ftq_ctx* c) {
     const long n = (long)c->W * c->M * c->M;
     k_c64_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->G32, c->G, n);
-    c->launches[FTQ_K_ESTIMATORS] += 1;
+    c->launches[FTQ_K_BRIDGE] += 1;
     c->g64_valid = true;
     return cudaGetLastError();
 }

@@ -1,0 +1,250 @@
+// Stabilisation of the mixed-precision chain with pre-pivoting.
+//
+// The right block is A_R = Y D_R T with Y = (B's since the last QR) Q_R in
+// FP32 and D_R, T^-1 in FP64.  Instead of pivoting at every Householder
+// step, the columns of C = Y D_R are sorted once by their norms (the
+// pre-pivoting of the GPU stratification work the paper cites for its
+// stabilisation): C Pi has decreasing column norms, Y is well conditioned
+// (a few B's times a unitary matrix) and the grading sits in D_R, so an
+// unpivoted Householder QR of C Pi separates the scales like QRCP does.
+//
+//   k_qr_prepiv64 (FP64, one block per walker): norms, sort, C Pi, Householder
+//       QR, D <- diag R, U = D^-1 R, T^-1 <- T^-1 Pi^T U^-1, permutation parity;
+//       the reflectors are also written in FP32, one reflector per row.
+//   k_form_q32 (FP32, one block per walker and 32-column panel): Q = H_0 ...
+//       H_{M-1} applied to the identity panel in shared memory, written into
+//       the chain planes as the new Y.
+#include <cmath>
+
+#include "complex_math.cuh"
+#include "ftq_internal.h"
+#include "mixed_common.cuh"
+
+namespace ftq {
+namespace {
+
+constexpr int QP = 32;   // columns per Q panel
+
+__device__ double bsum_d(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = sh[0];
+        for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i) acc += sh[i];
+        sh[0] = acc;
+    }
+    __syncthreads();
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_qr_prepiv64(const float* __restrict__ Ypl, double2* __restrict__ work,
+                              double2* __restrict__ work2, double2* __restrict__ DR, double2* __restrict__ Tinv,
+                              float2* __restrict__ VT, double* __restrict__ htau, double* __restrict__ ws,
+                              int* __restrict__ status, int M, Planes P, size_t wstride) {
+    extern __shared__ unsigned char smem_raw[];
+    double* cn = reinterpret_cast<double*>(smem_raw);      // [M] column norms of C
+    int* perm = reinterpret_cast<int*>(cn + M);            // [M] C Pi column j = C column perm[j]
+    unsigned char* seen = reinterpret_cast<unsigned char*>(perm + M);   // [M]
+    __shared__ double shd[32];
+    __shared__ double2 piv_u0;
+    __shared__ double piv_tau;
+    __shared__ int parity;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int w = blockIdx.x;
+    const long off = (long)w * M * M;
+    double2* C = work + off;
+    double2* XT = work2 + off;
+    double2* Ti = Tinv + off;
+    double2* Dw = DR + (long)w * M;
+    float2* V = VT + off;
+    const float* Yw = Ypl + wstride * w;
+
+    // column norms of C = Y D_R, then the rank of every column (descending
+    // norm, ties to the lower index)
+    for (int c = tid; c < M; c += nt) {
+        double s = 0.0;
+        for (int i = 0; i < M; ++i) {
+            float2 y = P.load(Yw, i, c);
+            s += (double)y.x * y.x + (double)y.y * y.y;
+        }
+        cn[c] = s * abs2(Dw[c]);
+    }
+    __syncthreads();
+    for (int c = tid; c < M; c += nt) {
+        int rank = 0;
+        const double v = cn[c];
+        for (int c2 = 0; c2 < M; ++c2) rank += (cn[c2] > v || (cn[c2] == v && c2 < c)) ? 1 : 0;
+        perm[rank] = c;
+        seen[c] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // parity of the permutation = (M - number of cycles) mod 2
+        int cycles = 0;
+        for (int c = 0; c < M; ++c) {
+            if (seen[c]) continue;
+            ++cycles;
+            for (int x = c; !seen[x]; x = perm[x]) seen[x] = 1;
+        }
+        parity = (M - cycles) & 1;
+    }
+    for (long e = tid; e < (long)M * M; e += nt) {
+        const int i = (int)(e / M), j = (int)(e % M);
+        const int src = perm[j];
+        const float2 y = P.load(Yw, i, src);
+        C[e] = cmul(make_double2(y.x, y.y), Dw[src]);
+    }
+    __syncthreads();
+
+    for (int j = 0; j < M; ++j) {
+        double s = 0.0;
+        for (int r = j + tid; r < M; r += nt) s += abs2(C[(long)r * M + j]);
+        s = bsum_d(s, shd);
+        if (tid == 0) {
+            const double2 al = C[(long)j * M + j];
+            const double sig = sqrt(s);
+            const double aa = sqrt(abs2(al));
+            const double2 beta = aa > 0.0 ? al * (-sig / aa) : make_double2(-sig, 0.0);
+            const double uhu = 2.0 * sig * (sig + aa);
+            piv_u0 = al - beta;
+            piv_tau = uhu > 0.0 ? 2.0 / uhu : 0.0;
+            htau[(long)w * M + j] = piv_tau;
+            C[(long)j * M + j] = beta;
+            if (!(sig > 0.0)) atomicOr(status, 1);
+        }
+        __syncthreads();
+        const double2 uj = piv_u0;
+        const double tj = piv_tau;
+        // reflector j in FP32 for the Q panels: V[j][r] = u_r, r >= j
+        for (int r = j + tid; r < M; r += nt) {
+            const double2 u = r == j ? uj : C[(long)r * M + j];
+            V[(long)j * M + r] = make_float2((float)u.x, (float)u.y);
+        }
+        for (int c = j + 1 + tid; c < M; c += nt) {
+            double2 acc = cmul(conj(uj), C[(long)j * M + c]);
+            for (int r = j + 1; r < M; ++r) acc = cfma(conj(C[(long)r * M + j]), C[(long)r * M + c], acc);
+            acc = acc * tj;
+            C[(long)j * M + c] = C[(long)j * M + c] - cmul(uj, acc);
+            for (int r = j + 1; r < M; ++r) C[(long)r * M + c] = C[(long)r * M + c] - cmul(C[(long)r * M + j], acc);
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < M; j += nt) Dw[j] = C[(long)j * M + j];
+    __syncthreads();
+    for (long e = tid; e < (long)M * M; e += nt) {
+        const int i = (int)(e / M), c = (int)(e % M);
+        if (c > i) C[e] = cdiv(C[e], C[(long)i * M + i]);
+    }
+    __syncthreads();
+    // T^-1 <- T^-1[:, perm] U^-1, one row per thread (XT column-major)
+    for (int i = tid; i < M; i += nt) {
+        for (int j = 0; j < M; ++j) {
+            double2 s = Ti[(long)i * M + perm[j]];
+            for (int m = 0; m < j; ++m) s = s - cmul(XT[(long)m * M + i], C[(long)m * M + j]);
+            XT[(long)j * M + i] = s;
+        }
+        for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
+    }
+    if (tid == 0) {
+        double* st = ws + 8L * w;
+        st[7] = (double)(((int)st[7]) ^ parity);
+    }
+}
+
+// Q[:, c0 .. c0+32) = H_0 ... H_{M-1} e_c, accumulated backwards in shared
+// memory (reflector j only touches rows >= j and columns >= j).
+__global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT, const double* __restrict__ htau,
+                                                 float* __restrict__ Ypl, int M, Planes P, size_t wstride) {
+    extern __shared__ unsigned char smem_raw[];
+    float2* Qp = reinterpret_cast<float2*>(smem_raw);     // [M][QP]
+    float2* ub = Qp + (size_t)M * QP;                     // [M]
+    __shared__ float2 part[8][QP];
+    __shared__ float2 wv[QP];
+    const int tid = threadIdx.x;
+    const int cc = tid & (QP - 1), g = tid >> 5;          // column in panel, row group (8 groups)
+    const int w = blockIdx.y;
+    const int c0 = blockIdx.x * QP;
+    const int ncol = min(QP, M - c0);
+    const long off = (long)w * M * M;
+    const float2* V = VT + off;
+    const double* tau = htau + (long)w * M;
+    for (int e = tid; e < M * QP; e += blockDim.x) {
+        const int r = e / QP, c = e % QP;
+        Qp[e] = make_float2(r == c0 + c ? 1.f : 0.f, 0.f);
+    }
+    __syncthreads();
+    const int jmax = c0 + ncol - 1;
+    for (int j = jmax; j >= 0; --j) {
+        for (int r = j + tid; r < M; r += blockDim.x) ub[r] = V[(long)j * M + r];
+        __syncthreads();
+        float2 s = make_float2(0.f, 0.f);
+        if (cc < ncol && c0 + cc >= j)
+            for (int r = j + g; r < M; r += 8) {
+                const float2 u = ub[r], q = Qp[r * QP + cc];
+                s.x = fmaf(u.x, q.x, fmaf(u.y, q.y, s.x));     // conj(u) q
+                s.y = fmaf(u.x, q.y, fmaf(-u.y, q.x, s.y));
+            }
+        part[g][cc] = s;
+        __syncthreads();
+        if (g == 0) {
+            float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t = t + part[k][cc];
+            const float tj = (float)tau[j];
+            wv[cc] = make_float2(t.x * tj, t.y * tj);
+        }
+        __syncthreads();
+        if (cc < ncol && c0 + cc >= j) {
+            const float2 wc = wv[cc];
+            for (int r = j + g; r < M; r += 8) {
+                const float2 u = ub[r];
+                float2 q = Qp[r * QP + cc];
+                q.x = fmaf(-u.x, wc.x, fmaf(u.y, wc.y, q.x));
+                q.y = fmaf(-u.x, wc.y, fmaf(-u.y, wc.x, q.y));
+                Qp[r * QP + cc] = q;
+            }
+        }
+        __syncthreads();
+    }
+    float* Yw = Ypl + wstride * w;
+    for (int e = tid; e < ncol * M; e += blockDim.x) {
+        const int c = e / M, i = e % M;
+        P.store(Yw, i, c0 + c, Qp[i * QP + c]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_qr_prepiv(ftq_ctx* c) {
+    const int M = c->M;
+    Planes P;
+    P.Kp = c->Kp;
+    P.part = (size_t)c->LD * 2 * c->Kp;
+    const size_t ws = 2 * P.part;
+    int nt = (M + 31) / 32 * 32;
+    nt = nt < 64 ? 64 : (nt > 1024 ? 1024 : nt);
+    const size_t sm1 = (sizeof(double) + sizeof(int) + 1) * M + 16;
+    {
+        LaunchScope ls(c, FTQ_K_QRCP);
+        k_qr_prepiv64<<<c->W, nt, sm1, c->stream>>>(c->Ypl, c->work, c->work2, c->DR, c->Tinv, c->w2_32, c->htau,
+                                                    c->wstate, c->status, M, P, ws);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t sm2 = sizeof(float2) * ((size_t)M * QP + M);
+    if (sm2 > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_form_q32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        if (e != cudaSuccess) return e;
+    }
+    LaunchScope ls(c, FTQ_K_BRIDGE);
+    k_form_q32<<<dim3((unsigned)((M + QP - 1) / QP), (unsigned)c->W), 256, sm2, c->stream>>>(c->w2_32, c->htau,
+                                                                                          c->Ypl, M, P, ws);
+    return cudaGetLastError();
+}
+
+}  // namespace ftq
