@@ -377,3 +377,91 @@ def weighted_estimate(results, constraint="phaseless"):
     ref = np.max(lwr)
     w = np.where(alive, np.exp(lwr - ref), 0.0)
     return np.sum(w * E.real) / np.sum(w), np.sum(w * Nn.real) / np.sum(w), np.sum(w)
+
+
+# ---------------------------------------------------------------- mu derivative
+def _with_mu(sys: UEG, mu):
+    """A shallow copy of `sys` whose propagator uses chemical potential mu
+    (B_T and mu_T unchanged, reading M)."""
+    import copy
+    s = copy.copy(sys)
+    s.mu = float(mu)
+    return s
+
+
+def path_with_fixed_bias(sys: UEG, fields, opts: Options, xbars):
+    """Propagate one walker with the force bias of every slice given
+    (xbars[k-1] for slice k) instead of computed from G."""
+    st = initial_state(sys)
+    for k in range(1, sys.n_slices + 1):
+        st, *_ = slice_step(sys, st, fields[k - 1], k, opts, xbar=xbars[k - 1])
+    return st
+
+
+def mu_observables(sys: UEG, fields, opts: Options = None, mu=None, xbars=None):
+    """Per-walker (ln w, alive, E_L, N_L) at tau = beta for chemical potential
+    mu; with `xbars` ([W][n][N_alpha]) the force bias is held at those values."""
+    opts = opts or Options()
+    s = sys if mu is None else _with_mu(sys, mu)
+    out = []
+    for w in range(fields.shape[1]):
+        if xbars is None:
+            r = propagate_walker(s, fields[:, w, :], opts, record=True)
+            out.append((r.logw, r.alive, r.energy, r.number, r.xbar_trace))
+        else:
+            st = path_with_fixed_bias(s, fields[:, w, :], opts, xbars[w])
+            E, Nn = local_energy(s, st.G)
+            out.append((st.logw, st.alive, E, Nn, None))
+    return out
+
+
+def _weighted(rows, mask):
+    lw = np.array([r[0].real for r in rows])
+    E = np.array([r[2].real for r in rows])
+    Nn = np.array([r[3].real for r in rows])
+    ref = np.max(lw[mask])
+    w = np.where(mask, np.exp(lw - ref), 0.0)
+    return np.sum(w * Nn) / np.sum(w), np.sum(w * E) / np.sum(w)
+
+
+def mu_derivative_fd(sys: UEG, fields, opts: Options = None, h=1e-4, frozen_bias=True):
+    """Central finite difference of the phaseless estimates <N> and <E> at
+    tau = beta with respect to mu, on the same draws x (Computational
+    Details: the interacting mu is tuned so that <N> = N-bar).
+
+    frozen_bias=True holds every slice's force bias at its value on the path
+    at mu (the derivative the library accumulates); False lets it follow
+    mu.  Walkers killed at mu - h, mu or mu + h but not at all three (a
+    cos theta = 0 crossing inside the stencil) are excluded; the count is
+    returned.  Returns dict(dN, dE, N, E, excluded)."""
+    opts = opts or Options()
+    base = mu_observables(sys, fields, opts)
+    xb = [r[4] for r in base] if frozen_bias else None
+    plus = mu_observables(sys, fields, opts, mu=sys.mu + h, xbars=xb)
+    minus = mu_observables(sys, fields, opts, mu=sys.mu - h, xbars=xb)
+    a0 = np.array([r[1] for r in base])
+    ap = np.array([r[1] for r in plus])
+    am = np.array([r[1] for r in minus])
+    mask = a0 & ap & am
+    excluded = int(np.sum(a0 != mask))
+    Np, Ep = _weighted(plus, mask)
+    Nm, Em = _weighted(minus, mask)
+    N0, E0 = _weighted(base, mask)
+    return dict(dN=(Np - Nm) / (2 * h), dE=(Ep - Em) / (2 * h), N=N0, E=E0, excluded=excluded, mask=mask)
+
+
+def mu_derivative_walkers_fd(sys: UEG, fields, opts: Options = None, h=1e-4):
+    """Per-walker central differences in mu at fixed draws and frozen force
+    bias: (d ln|w|, d E_L, d N_L, alive at mu-h, mu and mu+h) for every walker."""
+    opts = opts or Options()
+    base = mu_observables(sys, fields, opts)
+    xb = [r[4] for r in base]
+    plus = mu_observables(sys, fields, opts, mu=sys.mu + h, xbars=xb)
+    minus = mu_observables(sys, fields, opts, mu=sys.mu - h, xbars=xb)
+    out = []
+    for b, p, m in zip(base, plus, minus):
+        ok = b[1] and p[1] and m[1]
+        out.append(dict(dlogw=(p[0].real - m[0].real) / (2 * h) if ok else 0.0,
+                        dE=(p[2] - m[2]) / (2 * h), dN=(p[3] - m[3]) / (2 * h), alive=ok,
+                        logw=b[0].real, E=b[2], N=b[3]))
+    return out
