@@ -114,6 +114,21 @@ int ftq_green(ftq_ctx* ctx, void* G_dev);
  * Synchronises the stream. */
 int ftq_estimators(ftq_ctx* ctx, double* out_host, double* per_walker_dev);
 
+/* Derivatives of the estimates with respect to the chemical potential mu of
+ * B, at tau = beta, at fixed draws x and with every slice's force bias held at
+ * its value on the path (mu tuning: the interacting mu is tuned so that
+ * <N> = N-bar, Computational Details).  Every B carries exp(dtau mu), so
+ * d ln det(I + A_k)/dmu = k dtau (M - tr G(tau_k)) is accumulated during
+ * propagation into d ln|w|/dmu (phaseless: Re d ln S_k - tan(theta_k)
+ * Im d ln S_k); at tau = beta dG/dmu = -beta (I - G) G and
+ * d<O>/dmu = <dO + O d ln w> - <O><d ln w>.
+ *   out_host        host, 8 doubles: {Re d<N>/dmu, Re d<E>/dmu, Re <N>, Re <E>,
+ *                   n_alive, s, Im d<N>/dmu, Im d<E>/dmu}
+ *   per_walker_dev  nullable device float64 [W][8]: {d ln|w|/dmu, d arg w/dmu,
+ *                   Re dE/dmu, Im dE/dmu, Re dN/dmu, Im dN/dmu, 0, 0}
+ * FTQ_EINVAL unless the walkers are at tau = beta.  Synchronises the stream. */
+int ftq_mu_grad(ftq_ctx* ctx, double* out_host, double* per_walker_dev);
+
 /* Per-walker weights and determinants: device float64 [W][8]
  * {ln|w|, arg w, alive, Re ln det(I+A), Im ln det(I+A), Re gauss_k,
  *  Im gauss_k, unused} where gauss_k = x_k.xbar_k - xbar_k.xbar_k / 2 of the

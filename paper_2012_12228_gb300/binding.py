@@ -31,7 +31,7 @@ class Opts(ctypes.Structure):
 
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
-           "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc",
+           "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
            "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
            "border": 7}
@@ -67,6 +67,7 @@ def load_library(path=None):
     lib.ftq_profile.argtypes = [vp, i]
     lib.ftq_profile_read.argtypes = [vp, dp, i64p]
     lib.ftq_estimators_noalloc.argtypes = [i, i, d, vp, i, vp, vp]
+    lib.ftq_mu_grad.argtypes = [vp, dp, vp]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]
@@ -198,7 +199,73 @@ class Propagator:
     def launches(self):
         return sum(v[1] for v in self.profile_read().values())
 
+    def mu_grad(self, per_walker=True):
+        """d<N>/dmu and d<E>/dmu at tau = beta (fixed draws, frozen force bias)."""
+        t = self._torch
+        pw = t.empty((self.W, 8), dtype=t.float64, device="cuda") if per_walker else None
+        buf = (ctypes.c_double * 8)()
+        self._check(self.lib.ftq_mu_grad(self.h, buf, ctypes.c_void_p(pw.data_ptr()) if pw is not None else None),
+                    "ftq_mu_grad")
+        res = dict(dN=buf[0], dE=buf[1], N=buf[2], E=buf[3], n_alive=int(buf[4]), log_scale=buf[5],
+                   dN_imag=buf[6], dE_imag=buf[7])
+        if pw is not None:
+            res["per_walker"] = pw
+        return res
+
     def status(self):
         v = ctypes.c_int()
         self._check(self.lib.ftq_status(self.h, ctypes.byref(v)), "ftq_status")
         return v.value
+
+
+def _mu_estimates_impl():
+    import torch
+
+    class MuEstimates(torch.autograd.Function):
+        """(<N>, <E>) at tau = beta of a whole path on fixed fields as a
+        differentiable function of mu; the backward pass uses the library's
+        mu derivative (fixed draws, frozen force bias)."""
+
+        @staticmethod
+        def forward(ctx, mu, system, fields, walkers, options):
+            p = Propagator(system["N"], system["M"], system["rs"], system["theta"], system["dtau"],
+                           mu=float(mu), walkers=walkers, **(options or {}))
+            try:
+                p.propagate(fields)
+                g = p.mu_grad(per_walker=False)
+            finally:
+                p.close()
+            ctx.save_for_backward(torch.tensor([g["dN"], g["dE"]], dtype=torch.float64))
+            return torch.tensor([g["N"], g["E"]], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (d,) = ctx.saved_tensors
+            return (grad.to(torch.float64) * d).sum().reshape(()), None, None, None, None
+
+    return MuEstimates
+
+
+def mu_estimates(mu, system, fields, walkers, options=None):
+    """torch wrapper: returns tensor([<N>, <E>]) differentiable in the 0-d tensor mu."""
+    return _mu_estimates_impl().apply(mu, system, fields, walkers, options)
+
+
+def tune_mu(system, fields, walkers, target_n, mu0, iterations=4, options=None):
+    """Newton iteration mu <- mu - (<N> - N-bar) / (d<N>/dmu) on fixed fields
+    (replaces the bracketing and least-squares fit of the paper's mu tuning)."""
+    mu = float(mu0)
+    history = []
+    for _ in range(iterations):
+        p = Propagator(system["N"], system["M"], system["rs"], system["theta"], system["dtau"], mu=mu,
+                       walkers=walkers, **(options or {}))
+        try:
+            p.propagate(fields)
+            g = p.mu_grad(per_walker=False)
+        finally:
+            p.close()
+        history.append((mu, g["N"], g["dN"]))
+        if g["dN"] == 0:
+            break
+        mu -= (g["N"] - target_n) / g["dN"]
+    return mu, history

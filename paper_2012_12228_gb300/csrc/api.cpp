@@ -111,9 +111,9 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     chk(dalloc(c, &c->hh, W * M));
     chk(dalloc(c, &c->htau, W * M));
     chk(dalloc(c, &c->perm, W * M));
-    chk(dalloc(c, &c->wstate, W * 8));
-    chk(dalloc(c, &c->est, W * 8));
-    chk(dalloc(c, &c->red, 8));
+    chk(dalloc(c, &c->wstate, W * ftq::WSTRIDE));
+    chk(dalloc(c, &c->est, W * ftq::WSTRIDE));
+    chk(dalloc(c, &c->red, 16));
     chk(dalloc(c, &c->status, 1));
     const ftq::UegSetup& s = c->sys;
     std::vector<double> h(M), ksq(M), g0(M);
@@ -207,11 +207,24 @@ int ftq_estimators(ftq_ctx* c, double* out_host, double* per_walker_dev) {
     return FTQ_OK;
 }
 
+int ftq_mu_grad(ftq_ctx* c, double* out_host, double* per_walker_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
+    if (c->k != c->sys.n_slices)
+        return fail(c, FTQ_EINVAL, "the mu derivative is accumulated over a whole path: propagate to tau = beta first");
+    cudaError_t e = ftq::launch_mu_grad(c, per_walker_dev);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, c->red + 8, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mu_grad");
+    return FTQ_OK;
+}
+
 int ftq_weights(ftq_ctx* c, double* out_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
     if (!out_dev) return fail(c, FTQ_EINVAL, "out_dev must not be NULL");
-    cudaError_t e = cudaMemcpyAsync(out_dev, c->wstate, sizeof(double) * 8 * c->W, cudaMemcpyDeviceToDevice,
-                                    c->stream);
+    cudaError_t e = cudaMemcpy2DAsync(out_dev, sizeof(double) * 8, c->wstate, sizeof(double) * ftq::WSTRIDE,
+                                      sizeof(double) * 8, c->W, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "weights");
     return FTQ_OK;
 }

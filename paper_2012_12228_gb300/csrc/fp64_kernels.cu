@@ -73,8 +73,10 @@ __global__ void k_init_walkers(double2* DR, double* ws, int M, int W, double ld0
     int w = blockIdx.x;
     for (int i = threadIdx.x; i < M; i += blockDim.x) DR[(long)w * M + i] = make_double2(1.0, 0.0);
     if (threadIdx.x == 0) {
-        double* s = ws + 8L * w;
-        s[0] = 0.0; s[1] = 0.0; s[2] = 1.0; s[3] = ld0; s[4] = 0.0; s[5] = 0.0; s[6] = 0.0; s[7] = 0.0;
+        double* s = ws + (long)WSTRIDE * w;
+        for (int q = 0; q < WSTRIDE; ++q) s[q] = 0.0;
+        s[2] = 1.0;
+        s[3] = ld0;
     }
 }
 
@@ -117,8 +119,8 @@ __global__ void k_force_bias(const GT* __restrict__ G, const double* __restrict_
     }
     gauss = block_sum(gauss, sh);
     if (threadIdx.x == 0) {
-        ws[8L * w + 5] = gauss.x;
-        ws[8L * w + 6] = gauss.y;
+        ws[(long)WSTRIDE * w + 5] = gauss.x;
+        ws[(long)WSTRIDE * w + 6] = gauss.y;
     }
 }
 
@@ -312,7 +314,7 @@ __global__ void k_qrcp(const double2* __restrict__ Yin, double2* __restrict__ Qo
         for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
     }
     if (threadIdx.x == 0) {
-        double* s = ws + 8L * w;
+        double* s = ws + (long)WSTRIDE * w;
         s[7] = (double)(((int)s[7]) ^ nswap);
     }
 }
@@ -328,7 +330,7 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
                         double2* __restrict__ work2, double2* __restrict__ G,
                         const double* __restrict__ eps, double* __restrict__ ws,
                         int* __restrict__ status, int M, double lscale, double mu_T,
-                        int constraint, int update) {
+                        int constraint, int update, double kdt) {
     extern __shared__ unsigned char smem_raw[];
     double2* drs = reinterpret_cast<double2*>(smem_raw);     // [M]
     double2* invU = drs + M;                                 // [M]
@@ -430,29 +432,41 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
             Gw[(long)i * M + c] = g;
         }
     }
+    __syncthreads();
+    double2 trg = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < M; i += nt) trg = trg + Gw[(long)i * M + i];
+    trg = block_sum(trg, shc);
     if (threadIdx.x == 0) {
-        double* s = ws + 8L * w;
+        double* s = ws + (long)WSTRIDE * w;
         double2 ld = ldm;
         ld.x -= lsum;
         ld.y += kPi * (double)(nswap ^ ((int)s[7]));
         if (!isfinite(ld.x) || !isfinite(ld.y)) atomicOr(status, 1);
+        // d ln det(I + A_k)/dmu = k dtau (M - tr G(tau_k)): every B carries exp(dtau mu)
+        const double2 tk = make_double2(kdt * ((double)M - trg.x), -kdt * trg.y);
         if (update) {
             double2 lnS = make_double2(2.0 * (ld.x - s[3]), 2.0 * (ld.y - s[4]));
+            const double2 dlnS = make_double2(2.0 * (tk.x - s[9]), 2.0 * (tk.y - s[10]));
             double gr = s[5], gi = s[6];
             if (constraint == FTQ_FREE) {
                 s[0] += lnS.x + gr;
                 s[1] = remainder(s[1] + lnS.y + gi, 2.0 * kPi);
+                s[8] += dlnS.x;
+                s[11] += dlnS.y;
             } else if (s[2] > 0.5) {
                 double cth = cos(lnS.y);
                 if (cth <= 0.0) {
                     s[2] = 0.0;
                 } else {
                     s[0] += lnS.x + gr + log(cth);
+                    s[8] += dlnS.x - tan(lnS.y) * dlnS.y;   // d log cos(theta) = -tan(theta) d theta
                 }
             }
         }
         s[3] = ld.x;
         s[4] = remainder(ld.y, 2.0 * kPi);
+        s[9] = tk.x;
+        s[10] = tk.y;
     }
 }
 
@@ -502,8 +516,8 @@ __global__ void k_estimators(const double2* __restrict__ G, const double* __rest
     e1 = block_sum(e1, shc);
     e2 = block_sum(e2, shc);
     if (threadIdx.x == 0) {
-        const double* s = ws + 8L * w;
-        double* o = est + 8L * w;
+        const double* s = ws + (long)WSTRIDE * w;
+        double* o = est + (long)WSTRIDE * w;
         o[0] = s[0]; o[1] = s[1]; o[2] = s[2];
         o[3] = E_M + e1.x + e2.x; o[4] = e1.y + e2.y;
         o[5] = nsum.x; o[6] = nsum.y; o[7] = 0.0;
@@ -518,13 +532,13 @@ __global__ void k_reduce_walkers(const double* __restrict__ est, double* __restr
     double best = -INFINITY;
     int bi = W;
     for (int w = threadIdx.x; w < W; w += blockDim.x)
-        if (est[8L * w + 2] > 0.5 && est[8L * w] > best) { best = est[8L * w]; bi = w; }
+        if (est[(long)WSTRIDE * w + 2] > 0.5 && est[(long)WSTRIDE * w] > best) { best = est[(long)WSTRIDE * w]; bi = w; }
     int wm = block_argmax(best, bi, shv, shi);
-    double s = wm < W ? est[8L * wm] : 0.0;
+    double s = wm < W ? est[(long)WSTRIDE * wm] : 0.0;
     double2 sw = make_double2(0.0, 0.0), swe = sw, swn = sw;
     double nal = 0.0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
-        const double* o = est + 8L * w;
+        const double* o = est + (long)WSTRIDE * w;
         if (o[2] <= 0.5) continue;
         double m = exp(o[0] - s);
         double2 ww = make_double2(m * cos(o[1]), m * sin(o[1]));
@@ -636,7 +650,8 @@ cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     LaunchScope ls(c, FTQ_K_GREEN);
     k_green<<<c->W, nt, sm, c->stream>>>(Y, c->Tinv, c->DR, c->work, c->work2, c->G, c->tab.eps, c->wstate,
-                                        c->status, M, lscale, c->sys.mu_T, c->opts.constraint, update ? 1 : 0);
+                                        c->status, M, lscale, c->sys.mu_T, c->opts.constraint, update ? 1 : 0,
+                                        (double)k * c->sys.dtau);
     return cudaGetLastError();
 }
 
@@ -662,7 +677,8 @@ cudaError_t launch_estimators(ftq_ctx* c, double* per_walker) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (per_walker)
-        e = cudaMemcpyAsync(per_walker, c->est, sizeof(double) * 8 * c->W, cudaMemcpyDeviceToDevice, c->stream);
+        e = cudaMemcpy2DAsync(per_walker, sizeof(double) * 8, c->est, sizeof(double) * WSTRIDE, sizeof(double) * 8,
+                              c->W, cudaMemcpyDeviceToDevice, c->stream);
     return e;
 }
 

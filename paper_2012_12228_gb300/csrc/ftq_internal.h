@@ -10,6 +10,16 @@
 
 namespace ftq {
 
+// Per-walker state record, WSTRIDE doubles:
+//   [0] ln|w|  [1] arg w  [2] alive  [3] Re ln det(I+A)  [4] Im ln det
+//   [5] Re gauss_k  [6] Im gauss_k  [7] parity of det T
+//   [8] d ln|w|/dmu  [9] Re t_k  [10] Im t_k  (t_k = d ln det(I+A_k)/dmu)
+//   [11] d arg w/dmu  [12..15] unused
+// The per-walker estimator record uses the same stride:
+//   [0..2] as above, [3] Re E, [4] Im E, [5] Re N, [6] Im N, [7] unused,
+//   [8] d ln|w|/dmu, [9] d arg w/dmu, [10] Re dE, [11] Im dE, [12] Re dN, [13] Im dN
+constexpr int WSTRIDE = 16;
+
 // Static description of one UEG system (Sec. "Uniform Electron Gas" and
 // "Computational Details").  Built on the host once per context.
 struct UegSetup {
@@ -81,9 +91,9 @@ struct ftq_ctx {
     double2* hh = nullptr;        // Householder u_0 per column                [W][M]
     double* htau = nullptr;       // Householder tau                           [W][M]
     int* perm = nullptr;          // pivot permutation scratch                 [W][M]
-    double* wstate = nullptr;     // [W][8]: ln|w|, arg w, alive, Re ld, Im ld, Re gauss, Im gauss, tparity
-    double* est = nullptr;        // [W][8] per-walker estimators
-    double* red = nullptr;        // [8] reduced sums
+    double* wstate = nullptr;     // [W][WSTRIDE] per-walker state (layout above)
+    double* est = nullptr;        // [W][WSTRIDE] per-walker estimators
+    double* red = nullptr;        // [16] reduced sums (estimators, mu derivative)
     int* status = nullptr;        // latched numeric status
     size_t bytes = 0;
     std::string err;
@@ -151,6 +161,9 @@ cudaError_t mixed_chain(ftq_ctx* c);
 cudaError_t mixed_qrcp(ftq_ctx* c);
 cudaError_t mixed_green(ftq_ctx* c, int k);
 cudaError_t mixed_sync_g64(ftq_ctx* c);    // make G (complex128) hold G(tau) now
+
+// d<N>/dmu, d<E>/dmu at tau = beta (mu_grad.cu).
+cudaError_t launch_mu_grad(ftq_ctx* c, double* per_walker);
 
 // Blocked FP32 Green's function (green_blocked.cu); used while its shared
 // memory fits.

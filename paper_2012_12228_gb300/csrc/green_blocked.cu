@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
                                                    float2* __restrict__ work2, float2* __restrict__ G,
                                                    const double* __restrict__ eps, double* __restrict__ ws,
                                                    int* __restrict__ status, int M, double lscale, double mu_T,
-                                                   int constraint, Planes P, size_t wstride) {
+                                                   int constraint, Planes P, size_t wstride, double kdt) {
     extern __shared__ unsigned char smem_raw[];
     float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [M][NB]  panel / staged triangle block
     float2* Us = Ps + (size_t)M * NB;                          // [NB][M]  U12 rows of the current panel
@@ -355,24 +355,42 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
             if (c == i) g.x += 1.0f;
             Gw[(long)i * M + c] = g;
         }
+    __syncthreads();
+    double2 trg = make_double2(0.0, 0.0);
+    for (int i = tid; i < M; i += GT) {
+        const float2 g = Gw[(long)i * M + i];
+        trg = trg + make_double2(g.x, g.y);
+    }
+    trg = bsum(trg, shc);
     if (tid == 0) {
-        double* s = ws + 8L * w;
+        double* s = ws + (long)WSTRIDE * w;
         double2 ld = ldm;
         ld.x -= lsum;
         ld.y += kPi * (double)(nswap ^ ((int)s[7]));
         if (!isfinite(ld.x) || !isfinite(ld.y)) atomicOr(status, 1);
+        // d ln det(I + A_k)/dmu = k dtau (M - tr G(tau_k)): every B carries exp(dtau mu)
+        const double2 tk = make_double2(kdt * ((double)M - trg.x), -kdt * trg.y);
+        const double2 dlnS = make_double2(2.0 * (tk.x - s[9]), 2.0 * (tk.y - s[10]));
         double2 lnS = make_double2(2.0 * (ld.x - s[3]), 2.0 * (ld.y - s[4]));
         double gr = s[5], gi = s[6];
         if (constraint == FTQ_FREE) {
             s[0] += lnS.x + gr;
             s[1] = remainder(s[1] + lnS.y + gi, 2.0 * kPi);
+            s[8] += dlnS.x;
+            s[11] += dlnS.y;
         } else if (s[2] > 0.5) {
             double cth = cos(lnS.y);
-            if (cth <= 0.0) s[2] = 0.0;
-            else s[0] += lnS.x + gr + log(cth);
+            if (cth <= 0.0) {
+                s[2] = 0.0;
+            } else {
+                s[0] += lnS.x + gr + log(cth);
+                s[8] += dlnS.x - tan(lnS.y) * dlnS.y;   // d log cos(theta) = -tan(theta) d theta
+            }
         }
         s[3] = ld.x;
         s[4] = remainder(ld.y, 2.0 * kPi);
+        s[9] = tk.x;
+        s[10] = tk.y;
     }
 }
 
@@ -395,7 +413,8 @@ cudaError_t launch_green32b(ftq_ctx* c, int k) {
     nt = nt < 256 ? 256 : (nt > GT_MAX ? GT_MAX : nt);
     LaunchScope ls(c, FTQ_K_GREEN);
     k_green32b<<<c->W, nt, sm, c->stream>>>(c->Ypl, c->Tinv, c->DR, c->w32, c->w2_32, c->G32, c->tab.eps, c->wstate,
-                                           c->status, M, lscale, c->sys.mu_T, c->opts.constraint, P, 2 * P.part);
+                                           c->status, M, lscale, c->sys.mu_T, c->opts.constraint, P, 2 * P.part,
+                                           (double)k * c->sys.dtau);
     return cudaGetLastError();
 }
 

@@ -174,7 +174,7 @@ __global__ void k_green32(const float* __restrict__ Ypl, const double2* __restri
                           const double2* __restrict__ DR, float2* __restrict__ work, float2* __restrict__ work2,
                           float2* __restrict__ G, const double* __restrict__ eps, double* __restrict__ ws,
                           int* __restrict__ status, int M, double lscale, double mu_T, int constraint,
-                          Planes P, size_t wstride) {
+                          Planes P, size_t wstride, double kdt) {
     extern __shared__ unsigned char smem_raw[];
     float2* drs = reinterpret_cast<float2*>(smem_raw);      // [M]
     float2* invU = drs + M;                                 // [M]
@@ -285,24 +285,42 @@ __global__ void k_green32(const float* __restrict__ Ypl, const double2* __restri
             Gw[(long)i * M + c] = g;
         }
     }
+    __syncthreads();
+    double2 trg = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const float2 g = Gw[(long)i * M + i];
+        trg = trg + make_double2(g.x, g.y);
+    }
+    trg = block_sum(trg, shc);
     if (threadIdx.x == 0) {
-        double* s = ws + 8L * w;
+        double* s = ws + (long)WSTRIDE * w;
         double2 ld = ldm;
         ld.x -= lsum;
         ld.y += kPi * (double)(nswap ^ ((int)s[7]));
         if (!isfinite(ld.x) || !isfinite(ld.y)) atomicOr(status, 1);
+        // d ln det(I + A_k)/dmu = k dtau (M - tr G(tau_k)): every B carries exp(dtau mu)
+        const double2 tk = make_double2(kdt * ((double)M - trg.x), -kdt * trg.y);
+        const double2 dlnS = make_double2(2.0 * (tk.x - s[9]), 2.0 * (tk.y - s[10]));
         double2 lnS = make_double2(2.0 * (ld.x - s[3]), 2.0 * (ld.y - s[4]));
         double gr = s[5], gi = s[6];
         if (constraint == FTQ_FREE) {
             s[0] += lnS.x + gr;
             s[1] = remainder(s[1] + lnS.y + gi, 2.0 * kPi);
+            s[8] += dlnS.x;
+            s[11] += dlnS.y;
         } else if (s[2] > 0.5) {
             double cth = cos(lnS.y);
-            if (cth <= 0.0) s[2] = 0.0;
-            else s[0] += lnS.x + gr + log(cth);
+            if (cth <= 0.0) {
+                s[2] = 0.0;
+            } else {
+                s[0] += lnS.x + gr + log(cth);
+                s[8] += dlnS.x - tan(lnS.y) * dlnS.y;   // d log cos(theta) = -tan(theta) d theta
+            }
         }
         s[3] = ld.x;
         s[4] = remainder(ld.y, 2.0 * kPi);
+        s[9] = tk.x;
+        s[10] = tk.y;
     }
 }
 
@@ -400,7 +418,7 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
     LaunchScope ls(c, FTQ_K_GREEN);
     k_green32<<<c->W, nt, sm, c->stream>>>(c->Ypl, c->Tinv, c->DR, c->w32, c->w2_32, c->G32, c->tab.eps, c->wstate,
                                           c->status, M, lscale, c->sys.mu_T, c->opts.constraint, planes_of(c),
-                                          walker_stride(c));
+                                          walker_stride(c), (double)k * c->sys.dtau);
     c->g64_valid = false;
     return cudaGetLastError();
 }

@@ -151,7 +151,7 @@ __global__ void k_qr_prepiv64(const float* __restrict__ Ypl, double2* __restrict
         for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
     }
     if (tid == 0) {
-        double* st = ws + 8L * w;
+        double* st = ws + (long)WSTRIDE * w;
         st[7] = (double)(((int)st[7]) ^ parity);
     }
 }
