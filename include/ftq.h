@@ -66,6 +66,14 @@ typedef struct {
     double   force_bias_cap;   /* 0 = off (no cap is applied in this version)             */
 } ftq_opts;
 
+/* One system of a ragged batch (ftq_init_batch). */
+typedef struct {
+    int    N, M;
+    double rs, theta, mu, dtau;   /* as ftq_init_ueg; mu = NaN selects mu_T */
+    int    walkers;
+    int    reserved;              /* must be 0 */
+} ftq_system;
+
 /* Create a UEG system and W walkers at tau = 0 (A(0) = B_T^n).
  *   N      target electron number N-bar (even, 0 < N < 2M)
  *   M      plane-wave basis size; must be a closed-shell count (7, 19, 27, 33, 57, ...)
@@ -165,6 +173,32 @@ int ftq_query_f64(const ftq_ctx* ctx, int key, double* value);
  * half-space transfers [N_alpha/2][3] (int32, host buffers, caller-owned). */
 int ftq_basis(const ftq_ctx* ctx, int32_t* nvec_host);
 int ftq_transfers(const ftq_ctx* ctx, int32_t* q_host);
+
+/* Ragged batch: nsys (1..8) UEG systems of different basis size propagated
+ * together with the mixed-precision path (opts->precision must be FTQ_MIXED;
+ * opts->walkers is ignored, each system gives its own).  Every Horner step of
+ * the tensor-core chain runs as one persistent launch over the work items
+ * (system, walker, 64-row block, column tile) of all systems, and every
+ * ftq_batch_propagate call is captured into a CUDA graph that is updated and
+ * replayed as one launch.  The batch runs on its own stream, ordered after
+ * opts->cuda_stream on entry and before it on exit of every call.  The
+ * member systems are ordinary contexts (ftq_batch_member) for ftq_green,
+ * ftq_estimators, ftq_weights and ftq_mu_grad; they are destroyed with the
+ * batch.  Not a construct of the paper: it batches independent instances of
+ * its slice path (Sec. Computational Details: many independent simulations). */
+int ftq_init_batch(ftq_ctx** out, int nsys, const ftq_system* systems, const ftq_opts* opts);
+int ftq_batch_member(ftq_ctx* batch, int index, ftq_ctx** member);
+/* fields_dev: host array of nsys device pointers, member s float64
+ * [n_slices][W_s][N_alpha_s]; every member must stay within its own path. */
+int ftq_batch_propagate(ftq_ctx* batch, int n_slices, const double* const* fields_dev);
+
+/* Time the candidate column tilings (1, 2 or 3 column tiles per 64-row
+ * block) of the tensor-core chain on the context's own shapes and keep the
+ * fastest; for a batch every member is tuned.  choice / ms: nullable host
+ * arrays (one entry per system) receiving the chosen tile count and its time
+ * per Horner step.  Uses the chain's scratch buffers; walker state is not
+ * changed. */
+int ftq_autotune(ftq_ctx* ctx, int* choice, float* ms);
 
 /* Kernel classes for launch accounting and timing. */
 #define FTQ_K_FORCE_BIAS 0   /* force bias + shifted fields + V generator table   */

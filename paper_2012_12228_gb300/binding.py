@@ -29,9 +29,16 @@ class Opts(ctypes.Structure):
                 ("force_bias_cap", ctypes.c_double)]
 
 
+class System(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("rs", ctypes.c_double), ("theta", ctypes.c_double),
+                ("mu", ctypes.c_double), ("dtau", ctypes.c_double), ("walkers", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
+           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune",
            "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
            "border": 7}
@@ -68,6 +75,10 @@ def load_library(path=None):
     lib.ftq_profile_read.argtypes = [vp, dp, i64p]
     lib.ftq_estimators_noalloc.argtypes = [i, i, d, vp, i, vp, vp]
     lib.ftq_mu_grad.argtypes = [vp, dp, vp]
+    lib.ftq_init_batch.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(System), ctypes.POINTER(Opts)]
+    lib.ftq_batch_member.argtypes = [vp, i, ctypes.POINTER(vp)]
+    lib.ftq_batch_propagate.argtypes = [vp, i, ctypes.POINTER(vp)]
+    lib.ftq_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]
@@ -106,14 +117,36 @@ class Propagator:
         self.n_alpha = self.query("N_ALPHA")
         self.n_slices = self.query("N_SLICES")
 
+    @classmethod
+    def _member(cls, lib, handle, walkers):
+        """Non-owning view of a batch member context."""
+        import torch
+        obj = cls.__new__(cls)
+        obj._torch = torch
+        obj.lib = lib
+        obj.h = handle
+        obj._owned = False
+        obj.W = walkers
+        obj.M = obj.query("M")
+        obj.n_alpha = obj.query("N_ALPHA")
+        obj.n_slices = obj.query("N_SLICES")
+        return obj
+
+    def autotune(self):
+        """Pick the column tiling of the tensor-core chain by timing; returns (tiles, ms per step)."""
+        ch = (ctypes.c_int * 1)()
+        ms = (ctypes.c_float * 1)()
+        self._check(self.lib.ftq_autotune(self.h, ch, ms), "ftq_autotune")
+        return ch[0], ms[0]
+
     def _check(self, st, what):
         if st != 0:
             raise FTQError(f"{what}: {self.lib.ftq_last_error(self.h).decode()} (status {st})")
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and getattr(self, "_owned", True):
             self.lib.ftq_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -269,3 +302,81 @@ def tune_mu(system, fields, walkers, target_n, mu0, iterations=4, options=None):
             break
         mu -= (g["N"] - target_n) / g["dN"]
     return mu, history
+
+
+class Batch:
+    """Ragged batch of UEG systems (ftq_init_batch), mixed precision.
+
+    systems: list of dicts with N, M, rs, theta, dtau, walkers (mu optional)."""
+
+    def __init__(self, systems, stabilise_every=5, exp_order=6, stream=None, seed=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise FTQError("no CUDA device: the batch has no CPU path")
+        self._torch = torch
+        self.lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (System * len(systems))()
+        for k, sd in enumerate(systems):
+            arr[k] = System(sd["N"], sd["M"], sd["rs"], sd["theta"], float(sd.get("mu", float("nan"))),
+                            sd["dtau"], sd["walkers"], 0)
+        o = Opts(0, stabilise_every, exp_order, FTQ_MIXED, FTQ_PHASELESS, 0, seed,
+                 ctypes.c_void_p(self.stream.cuda_stream), 0.0)
+        h = ctypes.c_void_p()
+        st = self.lib.ftq_init_batch(ctypes.byref(h), len(systems), arr, ctypes.byref(o))
+        if st != 0:
+            raise FTQError(f"ftq_init_batch: {self.lib.ftq_last_error(None).decode()} (status {st})")
+        self.h = h
+        self.members = []
+        for k, sd in enumerate(systems):
+            mh = ctypes.c_void_p()
+            if self.lib.ftq_batch_member(self.h, k, ctypes.byref(mh)) != 0:
+                raise FTQError("ftq_batch_member failed")
+            self.members.append(Propagator._member(self.lib, mh, sd["walkers"]))
+
+    def propagate(self, fields):
+        """fields: list of CUDA float64 tensors [n][W_s][N_alpha_s], same n for all."""
+        t = self._torch
+        n = int(fields[0].shape[0])
+        ptrs = (ctypes.c_void_p * len(fields))()
+        for k, (f, m) in enumerate(zip(fields, self.members)):
+            if f.device.type != "cuda" or f.dtype != t.float64 or not f.is_contiguous():
+                raise FTQError("fields must be contiguous CUDA float64 tensors")
+            if f.shape[0] != n or f.shape[1] != m.W or f.shape[2] != m.n_alpha:
+                raise FTQError(f"fields[{k}] must have shape [{n}, {m.W}, {m.n_alpha}]")
+            ptrs[k] = f.data_ptr()
+        st = self.lib.ftq_batch_propagate(self.h, n, ptrs)
+        if st != 0:
+            raise FTQError(f"ftq_batch_propagate: {self.lib.ftq_last_error(self.h).decode()} (status {st})")
+
+    def autotune(self):
+        n = len(self.members)
+        ch = (ctypes.c_int * n)()
+        ms = (ctypes.c_float * n)()
+        st = self.lib.ftq_autotune(self.h, ch, ms)
+        if st != 0:
+            raise FTQError(f"ftq_autotune: {self.lib.ftq_last_error(self.h).decode()} (status {st})")
+        return [(ch[k], ms[k]) for k in range(n)]
+
+    def launches(self):
+        ms = (ctypes.c_double * K_COUNT)()
+        total = 0
+        for h in [self.h] + [m.h for m in self.members]:
+            nn = (ctypes.c_int64 * K_COUNT)()
+            self.lib.ftq_profile_read(h, ms, nn)
+            total += sum(nn)
+        return total
+
+    def close(self):
+        for m in self.members:
+            m.h = None
+        self.members = []
+        if getattr(self, "h", None):
+            self.lib.ftq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

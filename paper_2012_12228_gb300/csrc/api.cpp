@@ -41,7 +41,7 @@ void free_all(ftq_ctx* c) {
                     c->Ypl, c->zpl[0], c->zpl[1], c->G32, c->w32, c->w2_32,
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
-                    c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0};
+                    c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -108,6 +108,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     chk(dalloc(c, &c->zbuf[1], W * MM));
     chk(dalloc(c, &c->DR, W * M));
     chk(dalloc(c, &c->phi, W * c->nslot));
+    if (e == cudaSuccess) chk(cudaMemset(c->phi, 0, sizeof(double2) * W * c->nslot));
     chk(dalloc(c, &c->hh, W * M));
     chk(dalloc(c, &c->htau, W * M));
     chk(dalloc(c, &c->perm, W * M));
@@ -322,6 +323,10 @@ const char* ftq_last_error(const ftq_ctx* c) {
 void ftq_destroy(ftq_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    for (ftq_ctx* m : c->members) ftq_destroy(m);
+    c->members.clear();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->owns_stream && c->stream) cudaStreamDestroy(c->stream);
     for (auto& sp : c->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (auto ev : c->event_pool) cudaEventDestroy(ev);
     free_all(c);

@@ -22,7 +22,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "complex_math.cuh"
 #include "ftq_internal.h"
@@ -147,22 +150,37 @@ struct TcArgs {
     const double* us;
     const double* os;
     float alpha;
-    int M, nslot, Kp, LDc, NT, ktiles, ncols;
+    int M, nslot, Kp, LDc, NT, ktiles;
     int* status;
 };
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant__ CUtensorMap zmap, TcArgs p) {
+constexpr int MAXSYS = 8;
+
+// Up to MAXSYS systems in one launch: their chain tensor maps and arguments.
+struct TcBatch {
+    CUtensorMap maps[MAXSYS];
+    TcArgs args[MAXSYS];
+    int nsys;
+    int nt_max;         // largest N tile over the systems (shared-memory layout)
+    int nslot_max;
+    int ncols;          // TMEM columns allocated once per CTA
+};
+
+// Persistent kernel over a work list of items (system, walker, 64-row block,
+// column tile).  The stage counter g runs over all k tiles of all items a
+// CTA processes, so the mbarrier phases stay consistent from item to item.
+__global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant__ TcBatch tb,
+                                                          const int4* __restrict__ items, int nitems) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t tma_bar[2], mma_bar[2];
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rb = blockIdx.x, w = blockIdx.y;
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     unsigned char* base = smem_raw + pad;
     const uint32_t a_bytes = AROWS * KTILE * 4;
-    const uint32_t b_bytes = (uint32_t)p.NT * KTILE * 4;
-    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    const uint32_t bmax_bytes = (uint32_t)tb.nt_max * KTILE * 4;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * bmax_bytes;
     float2* phs = reinterpret_cast<float2*>(base + 2 * stage_bytes);
 
     if (tid == 0) {
@@ -173,94 +191,101 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(&tmem_sh, (uint32_t)p.ncols);
-    const double2* ph = p.phi + (long)w * p.nslot;
-    for (int i = tid; i < p.nslot; i += NTHREADS) {
-        double2 d = ph[i];
-        phs[i] = make_float2((float)d.x, (float)d.y);
-    }
+    if (warp == 0) tmem_alloc(&tmem_sh, (uint32_t)tb.ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_sh;
-    const uint32_t idesc = idesc_tf32(p.NT);
-    const int rows0 = rb * 64;
-    int last_tma = -1, last_mma = -1;   // meaningful in thread 0
+    int g = 0;                           // k tiles issued by this CTA so far
+    int last_tma = -1, last_mma = -1;    // meaningful in thread 0
     bool bad = false;
 
-    for (int kt = 0; kt < p.ktiles; ++kt) {
-        const int s = kt & 1, use = kt >> 1;
-        if (kt >= 2) {
-            bool ok = mbar_wait(&mma_bar[s], (uint32_t)((use - 1) & 1));
+    for (int item = blockIdx.x; item < nitems && !bad; item += gridDim.x) {
+        const int4 it = items[item];
+        const TcArgs& p = tb.args[it.x];
+        const CUtensorMap* map = &tb.maps[it.x];
+        const int w = it.y, rows0 = it.z * 64, col0 = it.w * p.NT;
+        const uint32_t b_bytes = (uint32_t)p.NT * KTILE * 4;
+        const uint32_t idesc = idesc_tf32(p.NT);
+        const double2* ph = p.phi + (long)w * p.nslot;
+        for (int i = tid; i < p.nslot; i += NTHREADS) {
+            const double2 d = ph[i];
+            phs[i] = make_float2((float)d.x, (float)d.y);
+        }
+        __syncthreads();
+        for (int kt = 0; kt < p.ktiles; ++kt, ++g) {
+            const int s = g & 1, use = g >> 1;
+            if (g >= 2) {
+                bool ok = mbar_wait(&mma_bar[s], (uint32_t)((use - 1) & 1));
+                if (__syncthreads_or(!ok)) { bad = true; break; }
+            }
+            unsigned char* Ahi = base + s * stage_bytes;
+            unsigned char* Alo = Ahi + a_bytes;
+            unsigned char* Bhi = Alo + a_bytes;
+            unsigned char* Blo = Bhi + bmax_bytes;
+            if (tid == 0) {
+                mbar_expect_tx(&tma_bar[s], 2 * b_bytes);
+                tma_load_2d(Bhi, map, kt * KTILE, (2 * w) * p.LDc + col0, &tma_bar[s]);
+                tma_load_2d(Blo, map, kt * KTILE, (2 * w + 1) * p.LDc + col0, &tma_bar[s]);
+                last_tma = g;
+            }
+            // A tile: row j (Re C) and row 64 + j (Im C) for complex row rows0 + j
+            const int kk = lane;
+            const int kg = kt * KTILE + kk;
+            const bool im_half = kg >= p.Kp;
+            const int kc = im_half ? kg - p.Kp : kg;
+            const ScaleF zsc((p.zs != nullptr && kc < p.M) ? p.zs[kc] : 1.0);
+            for (int j = warp; j < 64; j += NTHREADS / 32) {
+                const int i = rows0 + j;
+                float2 v = make_float2(0.f, 0.f);
+                if (i < p.M && kc < p.M) {
+                    v = phs[p.vidx[(long)i * p.M + kc]];
+                    v.x = zsc(v.x);
+                    v.y = zsc(v.y);
+                }
+                const float top = im_half ? -v.y : v.x;
+                const float bot = im_half ? v.x : v.y;
+                float h, l;
+                split_tf32(top, h, l);
+                uint32_t o = sw128_offset(j, kk);
+                *reinterpret_cast<float*>(Ahi + o) = h;
+                *reinterpret_cast<float*>(Alo + o) = l;
+                split_tf32(bot, h, l);
+                o = sw128_offset(64 + j, kk);
+                *reinterpret_cast<float*>(Ahi + o) = h;
+                *reinterpret_cast<float*>(Alo + o) = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                if (!mbar_wait(&tma_bar[s], (uint32_t)(use & 1))) {
+                    atomicOr(p.status, 2);
+                    abort_sh = 1;
+                } else {
+                    tc_fence_after();
+                    const uint64_t ah = sdesc_sw128(Ahi), al = sdesc_sw128(Alo);
+                    const uint64_t bh = sdesc_sw128(Bhi), bl = sdesc_sw128(Blo);
+#pragma unroll
+                    for (int k = 0; k < KTILE / 8; ++k) {
+                        const uint64_t dk = (uint64_t)((k * 32) >> 4);   // 8 tf32 = 32 bytes along the row
+                        mma_tf32(tmem, ah + dk, bh + dk, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                        mma_tf32(tmem, ah + dk, bl + dk, idesc, 1u);
+                        mma_tf32(tmem, al + dk, bh + dk, idesc, 1u);
+                    }
+                    mma_commit(&mma_bar[s]);
+                    last_mma = g;
+                }
+            }
+            __syncthreads();
+            if (abort_sh) { bad = true; break; }
+        }
+        if (bad) break;
+        {
+            const int last = g - 1;
+            bool ok = mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1));
             if (__syncthreads_or(!ok)) { bad = true; break; }
         }
-        unsigned char* Ahi = base + s * stage_bytes;
-        unsigned char* Alo = Ahi + a_bytes;
-        unsigned char* Bhi = Alo + a_bytes;
-        unsigned char* Blo = Bhi + b_bytes;
-        if (tid == 0) {
-            mbar_expect_tx(&tma_bar[s], 2 * b_bytes);
-            tma_load_2d(Bhi, &zmap, kt * KTILE, (2 * w) * p.LDc, &tma_bar[s]);
-            tma_load_2d(Blo, &zmap, kt * KTILE, (2 * w + 1) * p.LDc, &tma_bar[s]);
-            last_tma = kt;
-        }
-        // A tile: row j (Re C) and row 64 + j (Im C) for complex row rows0 + j
-        const int kk = lane;
-        const int kg = kt * KTILE + kk;
-        const bool im_half = kg >= p.Kp;
-        const int kc = im_half ? kg - p.Kp : kg;
-        const ScaleF zsc((p.zs != nullptr && kc < p.M) ? p.zs[kc] : 1.0);
-        for (int j = warp; j < 64; j += NTHREADS / 32) {
-            const int i = rows0 + j;
-            float2 v = make_float2(0.f, 0.f);
-            if (i < p.M && kc < p.M) {
-                v = phs[p.vidx[(long)i * p.M + kc]];
-                v.x = zsc(v.x);
-                v.y = zsc(v.y);
-            }
-            const float top = im_half ? -v.y : v.x;
-            const float bot = im_half ? v.x : v.y;
-            float h, l;
-            split_tf32(top, h, l);
-            uint32_t o = sw128_offset(j, kk);
-            *reinterpret_cast<float*>(Ahi + o) = h;
-            *reinterpret_cast<float*>(Alo + o) = l;
-            split_tf32(bot, h, l);
-            o = sw128_offset(64 + j, kk);
-            *reinterpret_cast<float*>(Ahi + o) = h;
-            *reinterpret_cast<float*>(Alo + o) = l;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            if (!mbar_wait(&tma_bar[s], (uint32_t)(use & 1))) {
-                atomicOr(p.status, 2);
-                abort_sh = 1;
-            } else {
-                tc_fence_after();
-                const uint64_t ah = sdesc_sw128(Ahi), al = sdesc_sw128(Alo);
-                const uint64_t bh = sdesc_sw128(Bhi), bl = sdesc_sw128(Blo);
-#pragma unroll
-                for (int k = 0; k < KTILE / 8; ++k) {
-                    const uint64_t dk = (uint64_t)((k * 32) >> 4);   // 8 tf32 = 32 bytes along the row
-                    mma_tf32(tmem, ah + dk, bh + dk, idesc, (kt > 0 || k > 0) ? 1u : 0u);
-                    mma_tf32(tmem, ah + dk, bl + dk, idesc, 1u);
-                    mma_tf32(tmem, al + dk, bh + dk, idesc, 1u);
-                }
-                mma_commit(&mma_bar[s]);
-                last_mma = kt;
-            }
-        }
-        __syncthreads();
-        if (abort_sh) { bad = true; break; }
-    }
-    if (!bad) {
-        const int last = p.ktiles - 1;
-        bool ok = mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1));
-        if (__syncthreads_or(!ok)) bad = true;
-    }
-    tc_fence_after();
-    if (!bad) {
+        tc_fence_after();
         const int r = (warp & 3) * 32 + lane;        // accumulator row = TMEM lane
         const int i = rows0 + (r & 63);
         const int part = r >> 6;                      // 0: Re C, 1: Im C
@@ -272,15 +297,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
         const size_t wstride = 2 * partoff;
         const float* U = p.Yu + wstride * w;
         float* O = p.out + wstride * w;
-        const int ncol = p.NT < p.M ? p.NT : p.M;
+        const int cend = min(col0 + p.NT, p.M);
         for (int ch = warp >> 2; ch * 16 < p.NT; ch += 2) {
             uint32_t v[16];
             tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ch * 16), v);
             if (row_ok) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const int c = ch * 16 + q;
-                    if (c < ncol) {
+                    const int c = col0 + ch * 16 + q;
+                    if (c < cend) {
                         const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
                         const float u = U[o] + U[partoff + o];
                         const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(u)));
@@ -292,17 +317,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
                 }
             }
         }
+        tc_fence_before();
+        __syncthreads();
     }
     tc_fence_before();
     __syncthreads();
     if (bad && tid == 0) {
-        atomicOr(p.status, 2);
+        atomicOr(tb.args[0].status, 2);
         if (last_tma >= 0) mbar_wait(&tma_bar[last_tma & 1], (uint32_t)((last_tma >> 1) & 1));
         if (last_mma >= 0) mbar_wait(&mma_bar[last_mma & 1], (uint32_t)((last_mma >> 1) & 1));
     }
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, (uint32_t)p.ncols);
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)tb.ncols);
 }
 
 // Output entries outside the MMA tile: rows [R, M) x all columns and
@@ -387,14 +414,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-// Tile plan for basis size M: rows covered by 64-row MMA blocks (R, possibly
-// padded above M) and the MMA N width (<= 256).
-void tc_plan(int M, int* R, int* NT) {
+// Tile plan for basis size M with nct column tiles: rows covered by 64-row
+// MMA blocks (R, possibly padded above M) and the MMA N width (<= 256).
+void tc_plan(int M, int nct, int* R, int* NT) {
     int rem = M % 64;
     if (rem == 0) *R = M;
     else if (M > 64 && rem <= 8) *R = M - rem;          // a thin border row band on CUDA cores
     else *R = (M + 63) / 64 * 64;                       // padded rows, not stored
-    *NT = M <= 256 ? (M + 15) / 16 * 16 : 256;
+    if (M <= 256 * nct) *NT = ((M + nct - 1) / nct + 15) / 16 * 16;
+    else *NT = 256;                                     // border columns [256 nct, M) on CUDA cores
 }
 
 bool tc_supported(int M) {
@@ -402,13 +430,15 @@ bool tc_supported(int M) {
     return encode_fn() != nullptr;
 }
 
+int tmem_cols(int NT) { return NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256)); }
+
 // One tensor map per chain buffer: [W * 2 * LDc rows] x [2 Kp floats],
-// boxes of 32 floats x NT rows, 128-byte swizzle.
+// boxes of 32 floats x NT rows, 128-byte swizzle; and the work list.
 cudaError_t tc_make_maps(ftq_ctx* c) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     int R, NT;
-    tc_plan(c->M, &R, &NT);
+    tc_plan(c->M, c->nct, &R, &NT);
     float* bufs[3] = {c->Ypl, c->zpl[0], c->zpl[1]};
     for (int b = 0; b < 3; ++b) {
         cuuint64_t dims[2] = {(cuuint64_t)(2 * c->Kp), (cuuint64_t)c->W * 2 * c->LD};
@@ -422,59 +452,193 @@ cudaError_t tc_make_maps(ftq_ctx* c) {
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
         c->tmap_buf[b] = bufs[b];
     }
-    return cudaSuccess;
+    std::vector<int4> items;
+    for (int w = 0; w < c->W; ++w)
+        for (int rb = 0; rb < R / 64; ++rb)
+            for (int ct = 0; ct < c->nct; ++ct) items.push_back(make_int4(0, w, rb, ct));
+    if (c->items) cudaFree(c->items);
+    c->items = nullptr;
+    cudaError_t e = cudaMalloc(&c->items, sizeof(int4) * items.size());
+    if (e != cudaSuccess) return e;
+    c->nitems = (int)items.size();
+    return cudaMemcpy(c->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
 }
+
+namespace {
+
+bool fill_args(ftq_ctx* c, const float* zin, float* out, const double* zs, const double* os, float alpha,
+               TcArgs* a, CUtensorMap* map, int* NTo) {
+    const CUtensorMap* m = nullptr;
+    for (int b = 0; b < 3; ++b)
+        if (c->tmap_buf[b] == zin) m = reinterpret_cast<const CUtensorMap*>(c->tmap[b]);
+    if (!m) return false;
+    *map = *m;
+    int R, NT;
+    tc_plan(c->M, c->nct, &R, &NT);
+    a->Yu = c->Ypl;
+    a->out = out;
+    a->phi = c->phi;
+    a->vidx = c->tab.vidx;
+    a->zs = zs;
+    a->us = c->tab.h;
+    a->os = os;
+    a->alpha = alpha;
+    a->M = c->M;
+    a->nslot = c->nslot;
+    a->Kp = c->Kp;
+    a->LDc = c->LD;
+    a->NT = NT;
+    a->ktiles = 2 * c->Kp / KTILE;
+    a->status = c->status;
+    *NTo = NT;
+    return true;
+}
+
+size_t tc_smem(int nt_max, int nslot_max) {
+    const size_t stage = 2 * (size_t)AROWS * KTILE * 4 + 2 * (size_t)nt_max * KTILE * 4;
+    return 1024 + 2 * stage + sizeof(float2) * nslot_max;
+}
+
+cudaError_t launch_items(ftq_ctx* timing_ctx, const TcBatch& tb, const int4* items, int nitems, cudaStream_t st) {
+    const size_t smem = tc_smem(tb.nt_max, tb.nslot_max);
+    static size_t smem_set = 0;
+    cudaError_t e = cudaSuccess;
+    if (smem > smem_set) {
+        e = cudaFuncSetAttribute(k_chain_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    int dev = 0, sms = 0, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_tc, NTHREADS, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int grid = std::min(nitems, sms * per_sm);
+    LaunchScope ls(timing_ctx, FTQ_K_CHAIN);
+    k_chain_tc<<<grid, NTHREADS, smem, st>>>(tb, items, nitems);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_border(ftq_ctx* c, const float* zin, float* out, const double* zs, const double* os, float alpha) {
+    int R, NT;
+    tc_plan(c->M, c->nct, &R, &NT);
+    if (R >= c->M && NT * c->nct >= c->M) return cudaSuccess;
+    Planes P;
+    P.Kp = c->Kp;
+    P.part = (size_t)c->LD * 2 * c->Kp;
+    const size_t bsm = sizeof(float2) * (c->M + c->nslot);
+    static size_t bsm_set = 48 * 1024;
+    if (bsm > bsm_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_chain_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+        if (e != cudaSuccess) return e;
+        bsm_set = bsm;
+    }
+    LaunchScope ls(c, FTQ_K_BORDER);
+    k_chain_border<<<c->W, 256, bsm, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, zs, c->tab.h, os, alpha,
+                                                 c->M, c->nslot, P, 2 * P.part, R, NT * c->nct);
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double* zs, const double* os,
                           float alpha) {
-    const CUtensorMap* map = nullptr;
-    for (int b = 0; b < 3; ++b)
-        if (c->tmap_buf[b] == zin) map = reinterpret_cast<const CUtensorMap*>(c->tmap[b]);
-    if (!map) return cudaErrorInvalidValue;
-    int R, NT;
-    tc_plan(c->M, &R, &NT);
-    TcArgs a;
-    a.Yu = c->Ypl;
-    a.out = out;
-    a.phi = c->phi;
-    a.vidx = c->tab.vidx;
-    a.zs = zs;
-    a.us = c->tab.h;
-    a.os = os;
-    a.alpha = alpha;
-    a.M = c->M;
-    a.nslot = c->nslot;
-    a.Kp = c->Kp;
-    a.LDc = c->LD;
-    a.NT = NT;
-    a.ktiles = 2 * c->Kp / KTILE;
-    a.ncols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
-    a.status = c->status;
-    const size_t stage = 2 * (size_t)AROWS * KTILE * 4 + 2 * (size_t)NT * KTILE * 4;
-    const size_t smem = 1024 + 2 * stage + sizeof(float2) * c->nslot;
-    cudaError_t e = cudaFuncSetAttribute(k_chain_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TcBatch tb;
+    std::memset(&tb, 0, sizeof(tb));
+    int NT;
+    if (!fill_args(c, zin, out, zs, os, alpha, &tb.args[0], &tb.maps[0], &NT)) return cudaErrorInvalidValue;
+    tb.nsys = 1;
+    tb.nt_max = NT;
+    tb.nslot_max = c->nslot;
+    tb.ncols = tmem_cols(NT);
+    cudaError_t e = launch_items(c, tb, c->items, c->nitems, c->stream);
     if (e != cudaSuccess) return e;
-    {
-        LaunchScope ls(c, FTQ_K_CHAIN);
-        k_chain_tc<<<dim3((unsigned)(R / 64), (unsigned)c->W), NTHREADS, smem, c->stream>>>(*map, a);
+    return launch_border(c, zin, out, zs, os, alpha);
+}
+
+// One Horner step for every member of a batch in one persistent launch.
+cudaError_t tc_chain_step_batch(ftq_ctx* b, const float* const* zin, float* const* out, int j, int p) {
+    TcBatch tb;
+    std::memset(&tb, 0, sizeof(tb));
+    const int ns = (int)b->members.size();
+    if (ns > MAXSYS) return cudaErrorInvalidValue;
+    tb.nsys = ns;
+    for (int s = 0; s < ns; ++s) {
+        ftq_ctx* c = b->members[s];
+        int NT;
+        if (!fill_args(c, zin[s], out[s], j == p ? c->tab.h : nullptr, j == 1 ? c->tab.h : nullptr, 1.0f / j,
+                       &tb.args[s], &tb.maps[s], &NT))
+            return cudaErrorInvalidValue;
+        tb.nt_max = std::max(tb.nt_max, NT);
+        tb.nslot_max = std::max(tb.nslot_max, c->nslot);
+        tb.ncols = std::max(tb.ncols, tmem_cols(NT));
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (R < c->M || NT < c->M) {
-        Planes P;
-        P.Kp = c->Kp;
-        P.part = (size_t)c->LD * 2 * c->Kp;
-        const size_t bsm = sizeof(float2) * (c->M + c->nslot);
-        if (bsm > 48 * 1024) {
-            e = cudaFuncSetAttribute(k_chain_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
-            if (e != cudaSuccess) return e;
-        }
-        LaunchScope ls(c, FTQ_K_BORDER);
-        k_chain_border<<<c->W, 256, bsm, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, zs, c->tab.h, os, alpha,
-                                                   c->M, c->nslot, P, 2 * P.part, R, NT);
-        e = cudaGetLastError();
+    cudaError_t e = launch_items(b, tb, b->items, b->nitems, b->stream);
+    for (int s = 0; s < ns && e == cudaSuccess; ++s) {
+        ftq_ctx* c = b->members[s];
+        e = launch_border(c, zin[s], out[s], j == p ? c->tab.h : nullptr, j == 1 ? c->tab.h : nullptr, 1.0f / j);
     }
     return e;
+}
+
+// Work list of a batch: every member's items, largest basis first.
+cudaError_t tc_batch_items(ftq_ctx* b) {
+    std::vector<int> order(b->members.size());
+    for (size_t s = 0; s < order.size(); ++s) order[s] = (int)s;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return b->members[x]->M > b->members[y]->M; });
+    std::vector<int4> items;
+    for (int s : order) {
+        ftq_ctx* c = b->members[s];
+        int R, NT;
+        tc_plan(c->M, c->nct, &R, &NT);
+        for (int w = 0; w < c->W; ++w)
+            for (int rb = 0; rb < R / 64; ++rb)
+                for (int ct = 0; ct < c->nct; ++ct) items.push_back(make_int4(s, w, rb, ct));
+    }
+    if (b->items) cudaFree(b->items);
+    b->items = nullptr;
+    cudaError_t e = cudaMalloc(&b->items, sizeof(int4) * items.size());
+    if (e != cudaSuccess) return e;
+    b->nitems = (int)items.size();
+    return cudaMemcpy(b->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+}
+
+// Time one Horner step (scratch output) for each column-tile count and keep
+// the fastest; returns the chosen count.
+cudaError_t tc_autotune(ftq_ctx* c, int* best_nct, float* best_ms) {
+    int best = c->nct;
+    float bms = 1e30f;
+    const int cands[3] = {1, 2, 3};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t e = cudaSuccess;
+    for (int nct : cands) {
+        int R, NT;
+        tc_plan(c->M, nct, &R, &NT);
+        if (nct > 1 && NT * (nct - 1) >= c->M) continue;   // an empty column tile
+        c->nct = nct;
+        e = tc_make_maps(c);
+        if (e != cudaSuccess) break;
+        e = tc_chain_step(c, c->Ypl, c->zpl[0], nullptr, nullptr, 1.0f);   // warm-up
+        if (e != cudaSuccess) break;
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3; ++r) tc_chain_step(c, c->Ypl, c->zpl[0], nullptr, nullptr, 1.0f);
+        cudaEventRecord(e1, c->stream);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        if (ms < bms) { bms = ms; best = nct; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    c->nct = best;
+    *best_nct = best;
+    *best_ms = bms;
+    return tc_make_maps(c);
 }
 
 }  // namespace ftq

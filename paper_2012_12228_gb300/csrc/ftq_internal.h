@@ -86,6 +86,14 @@ struct ftq_ctx {
     // TMA descriptors (CUtensorMap, 128 bytes) of the three chain buffers
     alignas(64) unsigned char tmap[3][128] = {};
     const float* tmap_buf[3] = {nullptr, nullptr, nullptr};
+    int nct = 1;                  // column tiles of the tensor-core chain (autotuned)
+    int4* items = nullptr;        // work list of the tensor-core chain
+    int nitems = 0;
+    // ragged batch: member systems (owned), CUDA graph of the last propagation
+    std::vector<ftq_ctx*> members;
+    cudaGraphExec_t gexec = nullptr;
+    bool use_graph = true;
+    bool owns_stream = false;
     double2* DR = nullptr;        // D_R                                       [W][M]
     double2* phi = nullptr;       // V generator table per walker              [W][nslot]
     double2* hh = nullptr;        // Householder u_0 per column                [W][M]
@@ -174,7 +182,10 @@ cudaError_t launch_green32b(ftq_ctx* c, int k);
 cudaError_t launch_qr_prepiv(ftq_ctx* c);
 
 // Tensor-core chain (chain_tc.cu).
-void tc_plan(int M, int* R, int* NT);
+void tc_plan(int M, int nct, int* R, int* NT);
+cudaError_t tc_chain_step_batch(ftq_ctx* b, const float* const* zin, float* const* out, int j, int p);
+cudaError_t tc_batch_items(ftq_ctx* b);
+cudaError_t tc_autotune(ftq_ctx* c, int* best_nct, float* best_ms);
 bool tc_supported(int M);
 cudaError_t tc_make_maps(ftq_ctx* c);
 cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double* zs, const double* os,

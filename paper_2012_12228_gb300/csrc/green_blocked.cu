@@ -403,8 +403,12 @@ size_t green32b_smem(int M) {
 cudaError_t launch_green32b(ftq_ctx* c, int k) {
     const int M = c->M;
     const size_t sm = green32b_smem(M);
-    cudaError_t e = cudaFuncSetAttribute(k_green32b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+    static size_t sm_set = 0;
+    if (sm > sm_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_green32b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        sm_set = sm;
+    }
     Planes P;
     P.Kp = c->Kp;
     P.part = (size_t)c->LD * 2 * c->Kp;

@@ -237,9 +237,11 @@ cudaError_t launch_qr_prepiv(ftq_ctx* c) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t sm2 = sizeof(float2) * ((size_t)M * QP + M);
-    if (sm2 > 48 * 1024) {
+    static size_t sm2_set = 48 * 1024;
+    if (sm2 > sm2_set) {
         e = cudaFuncSetAttribute(k_form_q32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
         if (e != cudaSuccess) return e;
+        sm2_set = sm2;
     }
     LaunchScope ls(c, FTQ_K_BRIDGE);
     k_form_q32<<<dim3((unsigned)((M + QP - 1) / QP), (unsigned)c->W), 256, sm2, c->stream>>>(c->w2_32, c->htau,

@@ -22,6 +22,16 @@ WORKLOADS = {
     "ueg_n66_m257": dict(N=66, M=257, rs=1.0, theta=0.0625, dtau=0.025, walkers=1024, seed=1239),
 }
 
+# Ragged batch: four (N, M) systems, each paired with one (r_s, Theta) so that
+# r_s in {0.5, 1, 2} and Theta in {0.0625, 0.125, 0.5} all occur; dtau = 0.05,
+# 256 walkers each (paths of 43, 87, 87 and 174 slices).
+RAGGED = [
+    dict(N=14, M=57, rs=0.5, theta=0.0625, dtau=0.05, walkers=256, seed=1301),
+    dict(N=38, M=123, rs=2.0, theta=0.5, dtau=0.05, walkers=256, seed=1302),
+    dict(N=54, M=171, rs=1.0, theta=0.125, dtau=0.05, walkers=256, seed=1303),
+    dict(N=66, M=257, rs=1.0, theta=0.0625, dtau=0.05, walkers=256, seed=1304),
+]
+
 
 def gaussian_fields(seed, n_slices, walkers, n_alpha, first_slice=0):
     """Standard-normal fields x[k][w][alpha] for slices first_slice..+n_slices.
