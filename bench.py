@@ -28,7 +28,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synthetic_inputs import WORKLOADS, gaussian_fields  # noqa: E402
+from synthetic_inputs import RAGGED, WORKLOADS, gaussian_fields  # noqa: E402
 
 METRIC = "walker-slices/sec at M=257 (mixed vs FP64, same GB300) at ≤1e-5 Ha/e error"
 WORKLOAD = "ueg_n66_m257"
@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the complex128 comparison")
     ap.add_argument("--no-compare", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed-vs-FP64 energy check")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--walkers", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", nargs=2, type=int, default=None, metavar=("WALKERS", "SLICES"),
@@ -202,13 +203,15 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     prop = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, stabilise_every=stab,
                           exp_order=p_order, precision=prec, stream=stream)
     M, na, n = prop.M, prop.n_alpha, prop.n_slices
+    tuned = prop.autotune() if precision == "mixed" else None
     total = warmup + steps
     if total * stab > n:
         raise SystemExit(f"warmup + steps must cover at most {n // stab} blocks of {stab} slices")
     seed = c["seed"] + 1000 * rank
     host = gaussian_fields(seed, total * stab, W, na).reshape(total, stab, W, na)
     fields = torch.from_numpy(host).to(dev)
-    out = {"M": M, "n_slices": n, "dtau": prop.query_f64("DTAU"), "walkers": W, "stab": stab, "p": p_order}
+    out = {"M": M, "n_slices": n, "dtau": prop.query_f64("DTAU"), "walkers": W, "stab": stab, "p": p_order,
+           "autotune": None if tuned is None else {"column_tiles": tuned[0], "ms_per_horner_step": tuned[1]}}
 
     for s in range(warmup):
         prop.propagate(fields[s])
@@ -281,6 +284,38 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     return out
 
 
+def measure_ragged(ftq, torch, dev, steps=4, warmup=3):
+    """Walker-slices/s of the ragged batch (four systems of M = 57, 123, 171,
+    257, 256 walkers each, one persistent tensor-core launch per Horner step,
+    CUDA-graph-captured blocks of 5 slices, autotuned column tiles)."""
+    b = ftq.Batch(RAGGED)
+    tuned = b.autotune()
+    stab = 5
+    fl = []
+    for sd, m in zip(RAGGED, b.members):
+        fl.append(torch.from_numpy(gaussian_fields(sd["seed"], (warmup + steps) * stab, sd["walkers"],
+                                                   m.n_alpha)).to(dev))
+    for s in range(warmup):
+        b.propagate([f[s * stab:(s + 1) * stab].contiguous() for f in fl])
+    torch.cuda.synchronize(dev)
+    l0 = b.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    for s in range(warmup, warmup + steps):
+        b.propagate([f[s * stab:(s + 1) * stab].contiguous() for f in fl])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    ws = sum(sd["walkers"] for sd in RAGGED) * stab * steps
+    res = {"value": ws / (ms / 1e3), "unit": "walker-slices/s", "ms_per_step": ms / steps, "steps": steps,
+           "warmup": warmup, "gpu_launches": b.launches() - l0, "graph": "one CUDA graph launch per step",
+           "systems": [dict(N=sd["N"], M=sd["M"], rs=sd["rs"], theta=sd["theta"], dtau=sd["dtau"],
+                            walkers=sd["walkers"], column_tiles=t[0]) for sd, t in zip(RAGGED, tuned)]}
+    b.close()
+    return res
+
+
 def accuracy_vs_fp64(ftq, torch, dev, W=32):
     """E/N at tau = beta of the mixed and the complex128 path on identical
     fields (whole path, W walkers)."""
@@ -341,6 +376,9 @@ def run_ours(args, rank, world, local_rank):
     acc = None
     if args.precision == "mixed" and not args.no_accuracy and rank == 0:
         acc = accuracy_vs_fp64(ftq, torch, dev)
+    ragged = None
+    if args.precision == "mixed" and not args.no_ragged and rank == 0:
+        ragged = measure_ragged(ftq, torch, dev)
     if rank != 0:
         return
     line = {
@@ -371,6 +409,10 @@ def run_ours(args, rank, world, local_rank):
                              "kernel_ms_per_step": comparison["kernel_ms_per_step"]}
     if acc:
         line["error_vs_fp64"] = acc
+    if ragged:
+        line["ragged_batch"] = ragged
+    if head.get("autotune"):
+        line["config"]["autotune"] = head["autotune"]
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

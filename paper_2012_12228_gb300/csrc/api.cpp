@@ -41,7 +41,8 @@ void free_all(ftq_ctx* c) {
                     c->Ypl, c->zpl[0], c->zpl[1], c->G32, c->w32, c->w2_32,
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
-                    c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items};
+                    c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
+                    c->tab.hf, c->phi32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -109,6 +110,10 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     chk(dalloc(c, &c->DR, W * M));
     chk(dalloc(c, &c->phi, W * c->nslot));
     if (e == cudaSuccess) chk(cudaMemset(c->phi, 0, sizeof(double2) * W * c->nslot));
+    if (opts->precision != FTQ_FP64) {
+        chk(dalloc(c, &c->phi32, W * c->nslot));
+        if (e == cudaSuccess) chk(cudaMemset(c->phi32, 0, sizeof(float2) * W * c->nslot));
+    }
     chk(dalloc(c, &c->hh, W * M));
     chk(dalloc(c, &c->htau, W * M));
     chk(dalloc(c, &c->perm, W * M));
@@ -134,6 +139,14 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         chk(upload(c, &c->tab.vq, s.vq));
         chk(upload(c, &c->tab.ksq, ksq));
         chk(upload(c, &c->tab.g0, g0));
+        chk(upload(c, &c->tab.pk, s.pk));
+        std::vector<float2> hf(M);
+        for (int i = 0; i < M; ++i) {
+            hf[i].x = (float)h[i];
+            hf[i].y = (float)(h[i] - (double)hf[i].x);
+        }
+        chk(upload(c, &c->tab.hf, hf));
+        chk(upload(c, &c->tab.qcube, s.qcube));
     }
     if (e == cudaSuccess && opts->precision == FTQ_MIXED) {
         if (!ftq::tc_supported(M)) {

@@ -11,9 +11,10 @@
 // V gathered from phi) and the B tile is the chain stored K-major (row c =
 // column c of Z as [Re | Im]), i.e. exactly the layout of the chain planes.
 //
-// One CTA = one walker x one block of 64 complex rows x all N columns (N <=
-// 256).  Two shared-memory stages: while the tensor core runs k tile t the
-// threads generate the A tile of t+1 and TMA fetches its B tile.  Every
+// Work item = one walker x one block of 64 complex rows x one column tile of
+// NT <= 256 columns.  A persistent CTA walks a list of items; two
+// shared-memory stages overlap the generation of A and the TMA of B for k
+// tile t+1 with the MMAs of tile t (warp specialisation below).  Every
 // mbarrier wait is bounded; on expiry the kernel sets bit 2 of the status
 // word, drains its own copies and MMAs (bounded) and frees TMEM.
 //
@@ -36,7 +37,6 @@ namespace {
 
 constexpr int KTILE = 32;            // floats per k tile = 128 bytes = one swizzle row
 constexpr int AROWS = 128;           // MMA M
-constexpr int NTHREADS = 256;
 constexpr long WAIT_LIMIT = 1L << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -136,21 +136,23 @@ __device__ __forceinline__ uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(AROWS >> 4) << 24);
 }
 
-// Element (r, k) of a 128 x 32 K-major tile in the 128-byte swizzled layout.
-__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
-}
+// Element (r, k) of a 128 x 32 K-major tile in the 128-byte swizzled layout
+// sits at byte (r >> 3) * 1024 + (r & 7) * 128 + (((k >> 2) ^ (r & 7)) & 7) * 16
+// + (k & 3) * 4; the generator below evaluates it incrementally.
 
 struct TcArgs {
     const float* Yu;
     float* out;
-    const double2* phi;
+    const float2* phi;            // FP32 field table [W][nslot]
     const uint16_t* vidx;
-    const double* zs;
-    const double* us;
-    const double* os;
+    const float2* zs;             // scales as (hi, lo) float pairs, nullable
+    const float2* us;
+    const float2* os;
+    const int* pk;                // packed basis coordinates [M]
+    const uint16_t* qcube;        // difference -> slot [qsize]
     float alpha;
     int M, nslot, Kp, LDc, NT, ktiles;
+    int qsize, qoff;
     int* status;
 };
 
@@ -163,18 +165,57 @@ struct TcBatch {
     int nsys;
     int nt_max;         // largest N tile over the systems (shared-memory layout)
     int nslot_max;
+    int qsize_max;
+    int m_max;
     int ncols;          // TMEM columns allocated once per CTA
 };
 
-// Persistent kernel over a work list of items (system, walker, 64-row block,
-// column tile).  The stage counter g runs over all k tiles of all items a
-// CTA processes, so the mbarrier phases stay consistent from item to item.
-__global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant__ TcBatch tb,
-                                                          const int4* __restrict__ items, int nitems) {
+// Persistent, warp-specialised kernel over a work list of items (system,
+// walker, 64-row block, column tile).
+//   warps 0..7 (256 threads): generate the A tile of every k tile into its
+//       shared-memory stage and arrive on afull[stage]; after an item's last
+//       MMA they run its epilogue (TMEM -> registers -> chain planes).
+//   warp 8, lane 0: waits for A (afull) and B (TMA), issues the 12 MMAs of a
+//       k tile, commits them to mma_bar[stage], and once the previous MMA
+//       group has drained prefetches the next B tile into the freed stage.
+// The stage counter g runs over all k tiles of all items a CTA processes, so
+// mbarrier phases stay consistent across items.  Every wait is bounded; on
+// expiry the kernel latches bit 2 of the status word, drains its own copies
+// and MMAs (bounded) and frees TMEM.
+constexpr int NGEN = 256;                 // generator / epilogue threads
+constexpr int NCTRL = 32;                 // control warp
+constexpr int NTHREADS_WS = NGEN + NCTRL;
+
+__device__ __forceinline__ void gen_barrier() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NGEN) : "memory");
+}
+
+// Bounded wait that also gives up once another warp has latched an abort;
+// the result is uniform over the calling warp's active lanes.
+__device__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+    bool ok = false;
+    for (long i = 0; i < WAIT_LIMIT && !ok; ++i) {
+        if (*abort_flag) break;
+        ok = mbar_try_wait(bar, parity);
+    }
+    ok = __all_sync(__activemask(), ok);
+    if (!ok && !*abort_flag) {
+        *abort_flag = 1;
+        atomicOr(status, 2);
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_constant__ TcBatch tb,
+                                                             const int4* __restrict__ items, int nitems) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t tma_bar[2], mma_bar[2];
+    __shared__ uint64_t tma_bar[2], mma_bar[2], afull[2];
     __shared__ uint32_t tmem_sh;
-    __shared__ int abort_sh;
+    __shared__ volatile int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     unsigned char* base = smem_raw + pad;
@@ -182,12 +223,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
     const uint32_t bmax_bytes = (uint32_t)tb.nt_max * KTILE * 4;
     const uint32_t stage_bytes = 2 * a_bytes + 2 * bmax_bytes;
     float2* phs = reinterpret_cast<float2*>(base + 2 * stage_bytes);
+    int* pks = reinterpret_cast<int*>(phs + tb.nslot_max);
+    uint16_t* qs = reinterpret_cast<uint16_t*>(pks + tb.m_max);
 
     if (tid == 0) {
-        mbar_init(&tma_bar[0], 1);
-        mbar_init(&tma_bar[1], 1);
-        mbar_init(&mma_bar[0], 1);
-        mbar_init(&mma_bar[1], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tma_bar[b], 1);
+            mbar_init(&mma_bar[b], 1);
+            mbar_init(&afull[b], NGEN / 32);
+        }
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -196,75 +240,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_sh;
-    int g = 0;                           // k tiles issued by this CTA so far
-    int last_tma = -1, last_mma = -1;    // meaningful in thread 0
-    bool bad = false;
 
-    for (int item = blockIdx.x; item < nitems && !bad; item += gridDim.x) {
-        const int4 it = items[item];
-        const TcArgs& p = tb.args[it.x];
-        const CUtensorMap* map = &tb.maps[it.x];
-        const int w = it.y, rows0 = it.z * 64, col0 = it.w * p.NT;
-        const uint32_t b_bytes = (uint32_t)p.NT * KTILE * 4;
-        const uint32_t idesc = idesc_tf32(p.NT);
-        const double2* ph = p.phi + (long)w * p.nslot;
-        for (int i = tid; i < p.nslot; i += NTHREADS) {
-            const double2 d = ph[i];
-            phs[i] = make_float2((float)d.x, (float)d.y);
-        }
-        __syncthreads();
-        for (int kt = 0; kt < p.ktiles; ++kt, ++g) {
-            const int s = g & 1, use = g >> 1;
-            if (g >= 2) {
-                bool ok = mbar_wait(&mma_bar[s], (uint32_t)((use - 1) & 1));
-                if (__syncthreads_or(!ok)) { bad = true; break; }
-            }
-            unsigned char* Ahi = base + s * stage_bytes;
-            unsigned char* Alo = Ahi + a_bytes;
-            unsigned char* Bhi = Alo + a_bytes;
-            unsigned char* Blo = Bhi + bmax_bytes;
-            if (tid == 0) {
-                mbar_expect_tx(&tma_bar[s], 2 * b_bytes);
-                tma_load_2d(Bhi, map, kt * KTILE, (2 * w) * p.LDc + col0, &tma_bar[s]);
-                tma_load_2d(Blo, map, kt * KTILE, (2 * w + 1) * p.LDc + col0, &tma_bar[s]);
-                last_tma = g;
-            }
-            // A tile: row j (Re C) and row 64 + j (Im C) for complex row rows0 + j
-            const int kk = lane;
-            const int kg = kt * KTILE + kk;
-            const bool im_half = kg >= p.Kp;
-            const int kc = im_half ? kg - p.Kp : kg;
-            const ScaleF zsc((p.zs != nullptr && kc < p.M) ? p.zs[kc] : 1.0);
-            for (int j = warp; j < 64; j += NTHREADS / 32) {
-                const int i = rows0 + j;
-                float2 v = make_float2(0.f, 0.f);
-                if (i < p.M && kc < p.M) {
-                    v = phs[p.vidx[(long)i * p.M + kc]];
-                    v.x = zsc(v.x);
-                    v.y = zsc(v.y);
-                }
-                const float top = im_half ? -v.y : v.x;
-                const float bot = im_half ? v.x : v.y;
-                float h, l;
-                split_tf32(top, h, l);
-                uint32_t o = sw128_offset(j, kk);
-                *reinterpret_cast<float*>(Ahi + o) = h;
-                *reinterpret_cast<float*>(Alo + o) = l;
-                split_tf32(bot, h, l);
-                o = sw128_offset(64 + j, kk);
-                *reinterpret_cast<float*>(Ahi + o) = h;
-                *reinterpret_cast<float*>(Alo + o) = l;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                if (!mbar_wait(&tma_bar[s], (uint32_t)(use & 1))) {
-                    atomicOr(p.status, 2);
-                    abort_sh = 1;
-                } else {
+    if (warp == NGEN / 32) {
+        // ------------------------------------------------ control warp
+        if (lane == 0) {
+            int* st = tb.args[0].status;
+            int g = 0, last_tma = -1, last_mma = -1;
+            auto issue_tma = [&](int4 it, int kt, int gi) {
+                const TcArgs& q = tb.args[it.x];
+                const int sg = gi & 1;
+                unsigned char* Bh = base + sg * stage_bytes + 2 * a_bytes;
+                mbar_expect_tx(&tma_bar[sg], 2u * (uint32_t)q.NT * KTILE * 4);
+                tma_load_2d(Bh, &tb.maps[it.x], kt * KTILE, (2 * it.y) * q.LDc + it.w * q.NT, &tma_bar[sg]);
+                tma_load_2d(Bh + bmax_bytes, &tb.maps[it.x], kt * KTILE, (2 * it.y + 1) * q.LDc + it.w * q.NT,
+                            &tma_bar[sg]);
+                last_tma = gi;
+            };
+            bool ok = true;
+            if ((int)blockIdx.x < nitems) issue_tma(items[blockIdx.x], 0, 0);
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int4 it = items[item];
+                const int4 nx = item + (int)gridDim.x < nitems ? items[item + gridDim.x] : make_int4(0, 0, 0, 0);
+                const TcArgs& p = tb.args[it.x];
+                const uint32_t idesc = idesc_tf32(p.NT);
+                for (int kt = 0; kt < p.ktiles && ok; ++kt, ++g) {
+                    const int s = g & 1, use = g >> 1;
+                    ok = mbar_wait_ab(&afull[s], (uint32_t)(use & 1), &abort_sh, st) &&
+                         mbar_wait_ab(&tma_bar[s], (uint32_t)(use & 1), &abort_sh, st);
+                    if (!ok) break;
                     tc_fence_after();
-                    const uint64_t ah = sdesc_sw128(Ahi), al = sdesc_sw128(Alo);
-                    const uint64_t bh = sdesc_sw128(Bhi), bl = sdesc_sw128(Blo);
+                    unsigned char* Ahi = base + s * stage_bytes;
+                    const uint64_t ah = sdesc_sw128(Ahi), al = sdesc_sw128(Ahi + a_bytes);
+                    const uint64_t bh = sdesc_sw128(Ahi + 2 * a_bytes), bl = sdesc_sw128(Ahi + 2 * a_bytes + bmax_bytes);
 #pragma unroll
                     for (int k = 0; k < KTILE / 8; ++k) {
                         const uint64_t dk = (uint64_t)((k * 32) >> 4);   // 8 tf32 = 32 bytes along the row
@@ -274,59 +281,126 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chain_tc(const __grid_constant_
                     }
                     mma_commit(&mma_bar[s]);
                     last_mma = g;
+                    // MMA(g - 1) frees stage s ^ 1 for the next B tile
+                    if (g >= 1) ok = mbar_wait_ab(&mma_bar[s ^ 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st);
+                    if (!ok) break;
+                    if (kt + 1 < p.ktiles) issue_tma(it, kt + 1, g + 1);
+                    else if (item + (int)gridDim.x < nitems) issue_tma(nx, 0, g + 1);
                 }
             }
-            __syncthreads();
-            if (abort_sh) { bad = true; break; }
+            if (!ok) {   // abort latched: drain this CTA's own copies and MMAs
+                if (last_tma >= 0) mbar_wait(&tma_bar[last_tma & 1], (uint32_t)((last_tma >> 1) & 1));
+                if (last_mma >= 0) mbar_wait(&mma_bar[last_mma & 1], (uint32_t)((last_mma >> 1) & 1));
+            }
         }
-        if (bad) break;
-        {
-            const int last = g - 1;
-            bool ok = mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1));
-            if (__syncthreads_or(!ok)) { bad = true; break; }
-        }
-        tc_fence_after();
-        const int r = (warp & 3) * 32 + lane;        // accumulator row = TMEM lane
-        const int i = rows0 + (r & 63);
-        const int part = r >> 6;                      // 0: Re C, 1: Im C
-        const bool row_ok = i < p.M;
-        const ScaleF usi(row_ok ? p.us[i] : 0.0);
-        const ScaleF osi((row_ok && p.os != nullptr) ? p.os[i] : 1.0);
-        const size_t rowlen = 2 * (size_t)p.Kp;
-        const size_t partoff = (size_t)p.LDc * rowlen;
-        const size_t wstride = 2 * partoff;
-        const float* U = p.Yu + wstride * w;
-        float* O = p.out + wstride * w;
-        const int cend = min(col0 + p.NT, p.M);
-        for (int ch = warp >> 2; ch * 16 < p.NT; ch += 2) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ch * 16), v);
-            if (row_ok) {
+    } else {
+        // ------------------------------------------------ generator / epilogue warps
+        // After an abort every generator warp still passes the same named
+        // barriers (loop bounds are uniform); only the work is skipped.
+        int* st = tb.args[0].status;
+        int g = 0;
+        int loaded_sys = -1;
+        // swizzled offsets: row j = warp + 8 t has (j & 7) = warp and (j >> 3) = t
+        const uint32_t off_top = (uint32_t)(warp * 128 + ((((lane >> 2) ^ warp) & 7) << 4) + (lane & 3) * 4);
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            const int4 it = items[item];
+            const TcArgs& p = tb.args[it.x];
+            const int w = it.y, rows0 = it.z * 64, col0 = it.w * p.NT;
+            const float2* ph = p.phi + (long)w * p.nslot;
+            for (int i = tid; i < p.nslot; i += NGEN) phs[i] = ph[i];
+            if (it.x != loaded_sys) {
+                for (int i = tid; i < p.M; i += NGEN) pks[i] = p.pk[i];
+                for (int i = tid; i < p.qsize; i += NGEN) qs[i] = p.qcube[i];
+                loaded_sys = it.x;
+            }
+            gen_barrier();
+            int prow[64 / (NGEN / 32)];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int c = col0 + ch * 16 + q;
-                    if (c < cend) {
+            for (int t = 0; t < 64 / (NGEN / 32); ++t) {
+                const int i = rows0 + warp + t * (NGEN / 32);
+                prow[t] = i < p.M ? pks[i] + p.qoff : -1;
+            }
+            for (int kt = 0; kt < p.ktiles; ++kt, ++g) {
+                const int s = g & 1, use = g >> 1;
+                if (g >= 2 && !mbar_wait_ab(&mma_bar[s], (uint32_t)((use - 1) & 1), &abort_sh, st)) continue;
+                if (abort_sh) continue;
+                unsigned char* Ahi = base + s * stage_bytes;
+                unsigned char* Alo = Ahi + a_bytes;
+                const int kg = kt * KTILE + lane;
+                const bool im_half = kg >= p.Kp;
+                const int kc = im_half ? kg - p.Kp : kg;
+                const ScaleF zsc((p.zs != nullptr && kc < p.M) ? p.zs[kc] : make_float2(1.f, 0.f));
+                const int pkc = kc < p.M ? pks[kc] : 0;
+#pragma unroll
+                for (int t = 0; t < 64 / (NGEN / 32); ++t) {
+                    float2 v = make_float2(0.f, 0.f);
+                    if (prow[t] >= 0 && kc < p.M) {
+                        v = phs[qs[prow[t] - pkc]];        // V[i][k] = phi(n_i - n_k)
+                        v.x = zsc(v.x);
+                        v.y = zsc(v.y);
+                    }
+                    const float top = im_half ? -v.y : v.x;
+                    const float bot = im_half ? v.x : v.y;
+                    float h, l;
+                    split_tf32(top, h, l);
+                    uint32_t o = off_top + (uint32_t)t * 1024u;          // element (warp + 8 t, lane)
+                    *reinterpret_cast<float*>(Ahi + o) = h;
+                    *reinterpret_cast<float*>(Alo + o) = l;
+                    split_tf32(bot, h, l);
+                    o += 8u * 1024u;                                     // row 64 + j
+                    *reinterpret_cast<float*>(Ahi + o) = h;
+                    *reinterpret_cast<float*>(Alo + o) = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&afull[s]);
+            }
+            // the item's accumulator: wait for its last MMA group
+            const bool acc_ok = mbar_wait_ab(&mma_bar[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st);
+            tc_fence_after();
+            const int r = (warp & 3) * 32 + lane;        // accumulator row = TMEM lane
+            const int i = rows0 + (r & 63);
+            const int part = r >> 6;                      // 0: Re C, 1: Im C
+            const bool row_ok = i < p.M;
+            const ScaleF usi(row_ok ? p.us[i] : make_float2(0.f, 0.f));
+            const ScaleF osi((row_ok && p.os != nullptr) ? p.os[i] : make_float2(1.f, 0.f));
+            const size_t rowlen = 2 * (size_t)p.Kp;
+            const size_t partoff = (size_t)p.LDc * rowlen;
+            const size_t wstride = 2 * partoff;
+            const float* __restrict__ U = p.Yu + wstride * w;
+            float* __restrict__ O = p.out + wstride * w;
+            const int cend = min(col0 + p.NT, p.M);
+            for (int ch = warp >> 2; acc_ok && ch * 16 < p.NT; ch += 2) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ch * 16), v);
+                if (row_ok) {
+                    float uh[16], ul[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {        // all loads first, then all stores
+                        const int c = col0 + ch * 16 + q;
                         const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
-                        const float u = U[o] + U[partoff + o];
-                        const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(u)));
-                        float h, l;
-                        split_tf32(val, h, l);
-                        O[o] = h;
-                        O[partoff + o] = l;
+                        uh[q] = c < cend ? U[o] : 0.f;
+                        ul[q] = c < cend ? U[partoff + o] : 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int c = col0 + ch * 16 + q;
+                        if (c < cend) {
+                            const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
+                            const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(uh[q] + ul[q])));
+                            float h, l;
+                            split_tf32(val, h, l);
+                            O[o] = h;
+                            O[partoff + o] = l;
+                        }
                     }
                 }
             }
+            tc_fence_before();
+            gen_barrier();        // all accumulator reads and generation done before the next item
         }
-        tc_fence_before();
-        __syncthreads();
     }
     tc_fence_before();
-    __syncthreads();
-    if (bad && tid == 0) {
-        atomicOr(tb.args[0].status, 2);
-        if (last_tma >= 0) mbar_wait(&tma_bar[last_tma & 1], (uint32_t)((last_tma >> 1) & 1));
-        if (last_mma >= 0) mbar_wait(&mma_bar[last_mma & 1], (uint32_t)((last_mma >> 1) & 1));
-    }
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, (uint32_t)tb.ncols);
@@ -349,16 +423,29 @@ __device__ __forceinline__ void border_store(float* O, const float* U, const Pla
     P.store(O, i, c, val);
 }
 
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// One warp per output entry, lanes over the contraction index (coalesced
+// reads of the chain rows), V from the shared difference cube.
 __global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ Zin, const float* __restrict__ Yu,
                                                      float* __restrict__ out, const double2* __restrict__ phi,
-                                                     const uint16_t* __restrict__ vidx,
+                                                     const int* __restrict__ pk, const uint16_t* __restrict__ qcube,
                                                      const double* __restrict__ zs, const double* __restrict__ us,
                                                      const double* __restrict__ os, float alpha, int M, int nslot,
-                                                     Planes P, size_t wstride, int R, int NT) {
+                                                     int qsize, int qoff, Planes P, size_t wstride, int R, int NT) {
     extern __shared__ unsigned char smem_raw[];
-    float2* vec = reinterpret_cast<float2*>(smem_raw);     // [M]: one row of V zs or one column of Z
+    float2* vec = reinterpret_cast<float2*>(smem_raw);     // [M]: one row of V zs or one column of Z zs
     float2* phs = vec + M;                                  // [nslot]
+    int* pks = reinterpret_cast<int*>(phs + nslot);         // [M]
+    uint16_t* qs = reinterpret_cast<uint16_t*>(pks + M);    // [qsize]
     const int w = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const float* Z = Zin + wstride * w;
     const float* U = Yu + wstride * w;
     float* O = out + wstride * w;
@@ -368,18 +455,21 @@ __global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ 
         const double2 d = ph[e];
         phs[e] = make_float2((float)d.x, (float)d.y);
     }
+    for (int e = threadIdx.x; e < M; e += blockDim.x) pks[e] = pk[e];
+    for (int e = threadIdx.x; e < qsize; e += blockDim.x) qs[e] = qcube[e];
     __syncthreads();
     for (int i = Rr; i < M; ++i) {              // border rows: (V zs)[i, :] Z
         for (int k = threadIdx.x; k < M; k += blockDim.x) {
             const ScaleF sk(zs ? zs[k] : 1.0);
-            const float2 v = phs[vidx[(long)i * M + k]];
+            const float2 v = phs[qs[pks[i] - pks[k] + qoff]];
             vec[k] = make_float2(sk(v.x), sk(v.y));
         }
         __syncthreads();
-        for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        for (int c = warp; c < M; c += nw) {
             float2 acc = make_float2(0.f, 0.f);
-            for (int k = 0; k < M; ++k) acc = cfma(vec[k], P.load(Z, k, c), acc);
-            border_store(O, U, P, us, os, alpha, i, c, acc);
+            for (int k = lane; k < M; k += 32) acc = cfma(vec[k], P.load(Z, k, c), acc);
+            acc = warp_sum(acc);
+            if (lane == 0) border_store(O, U, P, us, os, alpha, i, c, acc);
         }
         __syncthreads();
     }
@@ -390,10 +480,12 @@ __global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ 
             vec[k] = make_float2(sk(z.x), sk(z.y));
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < Rr; i += blockDim.x) {
+        for (int i = warp; i < Rr; i += nw) {
+            const int base = pks[i] + qoff;
             float2 acc = make_float2(0.f, 0.f);
-            for (int k = 0; k < M; ++k) acc = cfma(phs[vidx[(long)i * M + k]], vec[k], acc);
-            border_store(O, U, P, us, os, alpha, i, c, acc);
+            for (int k = lane; k < M; k += 32) acc = cfma(phs[qs[base - pks[k]]], vec[k], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) border_store(O, U, P, us, os, alpha, i, c, acc);
         }
         __syncthreads();
     }
@@ -477,11 +569,15 @@ bool fill_args(ftq_ctx* c, const float* zin, float* out, const double* zs, const
     tc_plan(c->M, c->nct, &R, &NT);
     a->Yu = c->Ypl;
     a->out = out;
-    a->phi = c->phi;
+    a->phi = c->phi32;
     a->vidx = c->tab.vidx;
-    a->zs = zs;
-    a->us = c->tab.h;
-    a->os = os;
+    a->zs = zs ? c->tab.hf : nullptr;     // the only scale the chain uses is h
+    a->us = c->tab.hf;
+    a->os = os ? c->tab.hf : nullptr;
+    a->pk = c->tab.pk;
+    a->qcube = c->tab.qcube;
+    a->qsize = c->sys.qS * c->sys.qS * c->sys.qS;
+    a->qoff = c->sys.qoff;
     a->alpha = alpha;
     a->M = c->M;
     a->nslot = c->nslot;
@@ -494,13 +590,13 @@ bool fill_args(ftq_ctx* c, const float* zin, float* out, const double* zs, const
     return true;
 }
 
-size_t tc_smem(int nt_max, int nslot_max) {
+size_t tc_smem(int nt_max, int nslot_max, int m_max, int qsize_max) {
     const size_t stage = 2 * (size_t)AROWS * KTILE * 4 + 2 * (size_t)nt_max * KTILE * 4;
-    return 1024 + 2 * stage + sizeof(float2) * nslot_max;
+    return 1024 + 2 * stage + sizeof(float2) * nslot_max + sizeof(int) * m_max + sizeof(uint16_t) * qsize_max;
 }
 
 cudaError_t launch_items(ftq_ctx* timing_ctx, const TcBatch& tb, const int4* items, int nitems, cudaStream_t st) {
-    const size_t smem = tc_smem(tb.nt_max, tb.nslot_max);
+    const size_t smem = tc_smem(tb.nt_max, tb.nslot_max, tb.m_max, tb.qsize_max);
     static size_t smem_set = 0;
     cudaError_t e = cudaSuccess;
     if (smem > smem_set) {
@@ -511,11 +607,11 @@ cudaError_t launch_items(ftq_ctx* timing_ctx, const TcBatch& tb, const int4* ite
     int dev = 0, sms = 0, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_tc, NTHREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_tc, NTHREADS_WS, smem);
     if (per_sm < 1) per_sm = 1;
     const int grid = std::min(nitems, sms * per_sm);
     LaunchScope ls(timing_ctx, FTQ_K_CHAIN);
-    k_chain_tc<<<grid, NTHREADS, smem, st>>>(tb, items, nitems);
+    k_chain_tc<<<grid, NTHREADS_WS, smem, st>>>(tb, items, nitems);
     return cudaGetLastError();
 }
 
@@ -526,7 +622,8 @@ cudaError_t launch_border(ftq_ctx* c, const float* zin, float* out, const double
     Planes P;
     P.Kp = c->Kp;
     P.part = (size_t)c->LD * 2 * c->Kp;
-    const size_t bsm = sizeof(float2) * (c->M + c->nslot);
+    const int qsize = c->sys.qS * c->sys.qS * c->sys.qS;
+    const size_t bsm = sizeof(float2) * (c->M + c->nslot) + sizeof(int) * c->M + sizeof(uint16_t) * qsize;
     static size_t bsm_set = 48 * 1024;
     if (bsm > bsm_set) {
         cudaError_t e = cudaFuncSetAttribute(k_chain_border, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
@@ -534,8 +631,9 @@ cudaError_t launch_border(ftq_ctx* c, const float* zin, float* out, const double
         bsm_set = bsm;
     }
     LaunchScope ls(c, FTQ_K_BORDER);
-    k_chain_border<<<c->W, 256, bsm, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.vidx, zs, c->tab.h, os, alpha,
-                                                 c->M, c->nslot, P, 2 * P.part, R, NT * c->nct);
+    k_chain_border<<<c->W, 256, bsm, c->stream>>>(zin, c->Ypl, out, c->phi, c->tab.pk, c->tab.qcube, zs, c->tab.h, os,
+                                                 alpha, c->M, c->nslot, qsize, c->sys.qoff, P, 2 * P.part, R,
+                                                 NT * c->nct);
     return cudaGetLastError();
 }
 
@@ -550,6 +648,8 @@ cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double
     tb.nsys = 1;
     tb.nt_max = NT;
     tb.nslot_max = c->nslot;
+    tb.m_max = c->M;
+    tb.qsize_max = tb.args[0].qsize;
     tb.ncols = tmem_cols(NT);
     cudaError_t e = launch_items(c, tb, c->items, c->nitems, c->stream);
     if (e != cudaSuccess) return e;
@@ -571,6 +671,8 @@ cudaError_t tc_chain_step_batch(ftq_ctx* b, const float* const* zin, float* cons
             return cudaErrorInvalidValue;
         tb.nt_max = std::max(tb.nt_max, NT);
         tb.nslot_max = std::max(tb.nslot_max, c->nslot);
+        tb.m_max = std::max(tb.m_max, c->M);
+        tb.qsize_max = std::max(tb.qsize_max, tb.args[s].qsize);
         tb.ncols = std::max(tb.ncols, tmem_cols(NT));
     }
     cudaError_t e = launch_items(b, tb, b->items, b->nitems, b->stream);

@@ -90,7 +90,7 @@ __device__ __forceinline__ double2 to_c128(float2 v) { return make_double2(v.x, 
 
 template <typename GT>
 __global__ void k_force_bias(const GT* __restrict__ G, const double* __restrict__ x,
-                             double2* __restrict__ phi, double* __restrict__ ws,
+                             double2* __restrict__ phi, float2* __restrict__ phi32, double* __restrict__ ws,
                              const int* __restrict__ pptr, const int* __restrict__ pa,
                              const int* __restrict__ pb, const double* __restrict__ cq,
                              int M, int nqh, double sdt) {
@@ -99,8 +99,12 @@ __global__ void k_force_bias(const GT* __restrict__ G, const double* __restrict_
     const GT* Gw = G + (long)w * M * M;
     const double* xw = x + (long)w * 2 * nqh;
     double2* ph = phi + (long)w * (2 * nqh + 1);
+    float2* ph32 = phi32 ? phi32 + (long)w * (2 * nqh + 1) : nullptr;
     double2 gauss = make_double2(0.0, 0.0);
-    if (threadIdx.x == 0) ph[0] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) {
+        ph[0] = make_double2(0.0, 0.0);
+        if (ph32) ph32[0] = make_float2(0.f, 0.f);
+    }
     for (int q = threadIdx.x; q < nqh; q += blockDim.x) {
         double2 rp = make_double2(0.0, 0.0), rm = make_double2(0.0, 0.0);
         for (int e = pptr[1 + 2 * q]; e < pptr[2 + 2 * q]; ++e) rp = rp - to_c128(Gw[(long)pb[e] * M + pa[e]]);
@@ -113,8 +117,13 @@ __global__ void k_force_bias(const GT* __restrict__ G, const double* __restrict_
         double2 yA = make_double2(xA - xbA.x, -xbA.y);
         double2 yB = make_double2(xB - xbB.x, -xbB.y);
         double2 iyB = times_i(yB);
-        ph[1 + 2 * q] = times_i(yA + iyB) * (sdt * c);
-        ph[2 + 2 * q] = times_i(yA - iyB) * (sdt * c);
+        const double2 pp = times_i(yA + iyB) * (sdt * c), pm = times_i(yA - iyB) * (sdt * c);
+        ph[1 + 2 * q] = pp;
+        ph[2 + 2 * q] = pm;
+        if (ph32) {
+            ph32[1 + 2 * q] = make_float2((float)pp.x, (float)pp.y);
+            ph32[2 + 2 * q] = make_float2((float)pm.x, (float)pm.y);
+        }
         gauss = gauss + xbA * xA - cmul(xbA, xbA) * 0.5 + xbB * xB - cmul(xbB, xbB) * 0.5;
     }
     gauss = block_sum(gauss, sh);
@@ -584,12 +593,13 @@ cudaError_t launch_init_walkers(ftq_ctx* c) {
 cudaError_t launch_force_bias_any(ftq_ctx* c, const double* x, const void* G, bool g32) {
     LaunchScope ls(c, FTQ_K_FORCE_BIAS);
     if (g32)
-        k_force_bias<float2><<<c->W, 256, 0, c->stream>>>(reinterpret_cast<const float2*>(G), x, c->phi, c->wstate,
+        k_force_bias<float2><<<c->W, 256, 0, c->stream>>>(reinterpret_cast<const float2*>(G), x, c->phi, c->phi32,
+                                                          c->wstate,
                                                           c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.cq,
                                                           c->M, c->sys.nq_half, std::sqrt(c->sys.dtau));
     else
         k_force_bias<double2><<<c->W, 256, 0, c->stream>>>(reinterpret_cast<const double2*>(G), x, c->phi,
-                                                           c->wstate, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b,
+                                                           c->phi32, c->wstate, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b,
                                                            c->tab.cq, c->M, c->sys.nq_half, std::sqrt(c->sys.dtau));
     return cudaGetLastError();
 }

@@ -36,6 +36,12 @@ struct UegSetup {
     // slot of the phi table addressed by (K', K): 0 for K' == K, 1 + 2q for
     // K' - K = +Q_q, 2 + 2q for K' - K = -Q_q.
     std::vector<uint16_t> vidx;   // [M][M]
+    // slot of a difference vector: V[i][k] = phi[qcube[pk[i] - pk[k] + qoff]]
+    // with pk[i] = nx S^2 + ny S + nz and S = 4 R + 1 (the cube of all
+    // differences of two basis vectors)
+    int qS = 0, qoff = 0;
+    std::vector<int> pk;          // [M]
+    std::vector<uint16_t> qcube;  // [S^3]
     // pairs (a, b) with n_a - n_b = Q for every slot, CSR by slot
     std::vector<int> pair_ptr;    // [2 nq_half + 2]
     std::vector<int> pair_a, pair_b;
@@ -56,6 +62,9 @@ struct DevTables {
     double* vq = nullptr;         // [nq_half]
     double* ksq = nullptr;        // |K|^2 [M]
     double* g0 = nullptr;         // diagonal of G(0) = (I + B_T^n)^-1 [M]
+    int* pk = nullptr;            // packed basis coordinates [M]
+    float2* hf = nullptr;         // h as float pairs (hi, lo) [M]
+    uint16_t* qcube = nullptr;    // difference -> slot [S^3]
 };
 
 }  // namespace ftq
@@ -96,6 +105,7 @@ struct ftq_ctx {
     bool owns_stream = false;
     double2* DR = nullptr;        // D_R                                       [W][M]
     double2* phi = nullptr;       // V generator table per walker              [W][nslot]
+    float2* phi32 = nullptr;      // the same table in FP32 (mixed path)       [W][nslot]
     double2* hh = nullptr;        // Householder u_0 per column                [W][M]
     double* htau = nullptr;       // Householder tau                           [W][M]
     int* perm = nullptr;          // pivot permutation scratch                 [W][M]

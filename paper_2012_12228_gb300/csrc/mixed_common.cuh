@@ -28,6 +28,7 @@ struct ScaleF {
         hi = (float)s;
         lo = (float)(s - (double)hi);
     }
+    __device__ __forceinline__ explicit ScaleF(float2 p) : hi(p.x), lo(p.y) {}
     __device__ __forceinline__ float operator()(float x) const { return fmaf(lo, x, hi * x); }
 };
 

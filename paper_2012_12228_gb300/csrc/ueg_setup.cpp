@@ -122,6 +122,15 @@ std::string build_ueg(UegSetup& s, int N, int M, double rs, double theta, double
             pairs[slot].push_back({i, j});
         }
     if (nslot > 65535) return "too many momentum transfers for 16-bit slots";
+    // difference cube: every n_i - n_k has components in [-2R, 2R]
+    s.qS = 4 * s.R + 1;
+    const int S = s.qS;
+    s.qoff = 2 * s.R * (S * S + S + 1);
+    s.pk.resize(M);
+    for (int i = 0; i < M; ++i) s.pk[i] = ball[i][0] * S * S + ball[i][1] * S + ball[i][2];
+    s.qcube.assign((size_t)S * S * S, 0);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) s.qcube[(size_t)(s.pk[i] - s.pk[j] + s.qoff)] = s.vidx[(size_t)i * M + j];
     s.pair_ptr.assign(nslot + 1, 0);
     s.pair_a.clear();
     s.pair_b.clear();
