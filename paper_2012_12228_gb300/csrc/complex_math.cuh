@@ -12,6 +12,10 @@ __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
     return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
+// c - a * b with four fused multiply-adds
+__host__ __device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
 __host__ __device__ __forceinline__ double2 conj(double2 a) { return make_double2(a.x, -a.y); }
 __host__ __device__ __forceinline__ double2 times_i(double2 a) { return make_double2(-a.y, a.x); }
 __host__ __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }

@@ -283,8 +283,8 @@ __global__ void k_qrcp(const double2* __restrict__ Yin, double2* __restrict__ Qo
             double2 s = cmul(conj(uj), C[(long)j * M + c]);
             for (int r = j + 1; r < M; ++r) s = cfma(conj(C[(long)r * M + j]), C[(long)r * M + c], s);
             s = s * tj;
-            C[(long)j * M + c] = C[(long)j * M + c] - cmul(uj, s);
-            for (int r = j + 1; r < M; ++r) C[(long)r * M + c] = C[(long)r * M + c] - cmul(C[(long)r * M + j], s);
+            C[(long)j * M + c] = cfms(uj, s, C[(long)j * M + c]);
+            for (int r = j + 1; r < M; ++r) C[(long)r * M + c] = cfms(C[(long)r * M + j], s, C[(long)r * M + c]);
         }
         __syncthreads();
     }
@@ -301,8 +301,8 @@ __global__ void k_qrcp(const double2* __restrict__ Yin, double2* __restrict__ Qo
             double2 s = cmul(conj(uj), Q[(long)j * M + c]);
             for (int r = j + 1; r < M; ++r) s = cfma(conj(C[(long)r * M + j]), Q[(long)r * M + c], s);
             s = s * tj;
-            Q[(long)j * M + c] = Q[(long)j * M + c] - cmul(uj, s);
-            for (int r = j + 1; r < M; ++r) Q[(long)r * M + c] = Q[(long)r * M + c] - cmul(C[(long)r * M + j], s);
+            Q[(long)j * M + c] = cfms(uj, s, Q[(long)j * M + c]);
+            for (int r = j + 1; r < M; ++r) Q[(long)r * M + c] = cfms(C[(long)r * M + j], s, Q[(long)r * M + c]);
         }
         __syncthreads();
     }
@@ -317,7 +317,7 @@ __global__ void k_qrcp(const double2* __restrict__ Yin, double2* __restrict__ Qo
     for (int i = threadIdx.x; i < M; i += nt) {
         for (int j = 0; j < M; ++j) {
             double2 s = Ti[(long)i * M + perm[j]];
-            for (int m = 0; m < j; ++m) s = s - cmul(XT[(long)m * M + i], C[(long)m * M + j]);
+            for (int m = 0; m < j; ++m) s = cfms(XT[(long)m * M + i], C[(long)m * M + j], s);
             XT[(long)j * M + i] = s;
         }
         for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
@@ -412,7 +412,7 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
         __syncthreads();
         for (int c = j + 1 + threadIdx.x; c < M; c += nt) {
             const double2 u = A[(long)j * M + c];
-            for (int i = j + 1; i < M; ++i) A[(long)i * M + c] = A[(long)i * M + c] - cmul(A[(long)i * M + j], u);
+            for (int i = j + 1; i < M; ++i) A[(long)i * M + c] = cfms(A[(long)i * M + j], u, A[(long)i * M + c]);
         }
         __syncthreads();
     }
@@ -426,12 +426,12 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
     for (int i = threadIdx.x; i < M; i += nt) {
         for (int j = 0; j < M; ++j) {
             double2 s = cmul(Yw[(long)i * M + j], drs[j]);
-            for (int m = 0; m < j; ++m) s = s - cmul(XT[(long)m * M + i], A[(long)m * M + j]);
+            for (int m = 0; m < j; ++m) s = cfms(XT[(long)m * M + i], A[(long)m * M + j], s);
             XT[(long)j * M + i] = cmul(s, invU[j]);
         }
         for (int j = M - 2; j >= 0; --j) {
             double2 s = XT[(long)j * M + i];
-            for (int m = j + 1; m < M; ++m) s = s - cmul(XT[(long)m * M + i], A[(long)m * M + j]);
+            for (int m = j + 1; m < M; ++m) s = cfms(XT[(long)m * M + i], A[(long)m * M + j], s);
             XT[(long)j * M + i] = s;
         }
         for (int m = 0; m < M; ++m) {

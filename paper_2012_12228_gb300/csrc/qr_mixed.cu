@@ -129,8 +129,8 @@ __global__ void k_qr_prepiv64(const float* __restrict__ Ypl, double2* __restrict
             double2 acc = cmul(conj(uj), C[(long)j * M + c]);
             for (int r = j + 1; r < M; ++r) acc = cfma(conj(C[(long)r * M + j]), C[(long)r * M + c], acc);
             acc = acc * tj;
-            C[(long)j * M + c] = C[(long)j * M + c] - cmul(uj, acc);
-            for (int r = j + 1; r < M; ++r) C[(long)r * M + c] = C[(long)r * M + c] - cmul(C[(long)r * M + j], acc);
+            C[(long)j * M + c] = cfms(uj, acc, C[(long)j * M + c]);
+            for (int r = j + 1; r < M; ++r) C[(long)r * M + c] = cfms(C[(long)r * M + j], acc, C[(long)r * M + c]);
         }
         __syncthreads();
     }
@@ -145,7 +145,7 @@ __global__ void k_qr_prepiv64(const float* __restrict__ Ypl, double2* __restrict
     for (int i = tid; i < M; i += nt) {
         for (int j = 0; j < M; ++j) {
             double2 s = Ti[(long)i * M + perm[j]];
-            for (int m = 0; m < j; ++m) s = s - cmul(XT[(long)m * M + i], C[(long)m * M + j]);
+            for (int m = 0; m < j; ++m) s = cfms(XT[(long)m * M + i], C[(long)m * M + j], s);
             XT[(long)j * M + i] = s;
         }
         for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
