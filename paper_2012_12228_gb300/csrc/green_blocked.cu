@@ -8,7 +8,9 @@
 //       applied to the rest of the matrix column by column; U12 = L11^-1 A12
 //       one column per thread; A22 -= L21 U12 in 4 x 4 complex micro-tiles.
 //   X U = Y D_Rs and W L = X: 32-column blocks, one row per thread, the
-//       block of U (or L) staged in shared memory and broadcast.
+//       block of U (or L) staged in shared memory and broadcast; X is stored
+//       column-major so that a warp's loads of one column are contiguous.
+//   G is written through 32 x 33 shared tiles with the inverse pivot order.
 //
 // One thread block per walker (ceil(M/32) warps, 256..384 threads, so that
 // the solves take one row per thread); matrices live in L2 / HBM.
@@ -22,6 +24,11 @@ namespace ftq {
 namespace {
 
 constexpr int NB = 32;
+constexpr int PSTR = NB + 1;   // padded row stride of the LU panel (column reads conflict-free)
+constexpr int TILE = 32 * 33;  // one padded 32 x 32 transpose tile
+
+// Length of the U12 region, which also holds the transpose tile.
+__host__ __device__ __forceinline__ int us_len(int M) { return NB * M > TILE ? NB * M : TILE; }
 constexpr int GT_MAX = 384;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -48,6 +55,9 @@ __device__ T bsum(T v, T* sh) {
     return r;
 }
 
+// Block-wide argmax (ties to the lower index) with one barrier: every thread
+// reduces the per-warp results itself.  The caller separates consecutive
+// calls by at least one barrier.
 __device__ int bargmax(float val, int idx, float* shv, int* shi) {
     for (int o = 16; o > 0; o >>= 1) {
         float ov = __shfl_down_sync(0xffffffffu, val, o);
@@ -55,20 +65,13 @@ __device__ int bargmax(float val, int idx, float* shv, int* shi) {
         if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
     if (lane == 0) { shv[wid] = val; shi[wid] = idx; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float bv = shv[0];
-        int bi = shi[0];
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
-            if (shv[i] > bv || (shv[i] == bv && shi[i] < bi)) { bv = shv[i]; bi = shi[i]; }
-        shi[0] = bi;
-    }
-    __syncthreads();
-    int r = shi[0];
-    __syncthreads();
-    return r;
+    float bv = shv[0];
+    int bi = shi[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i)
+        if (shv[i] > bv || (shv[i] == bv && shi[i] < bi)) { bv = shv[i]; bi = shi[i]; }
+    return bi;
 }
 
 __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict__ Ypl, const double2* __restrict__ Tinv,
@@ -78,9 +81,9 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
                                                    int* __restrict__ status, int M, double lscale, double mu_T,
                                                    int constraint, Planes P, size_t wstride, double kdt) {
     extern __shared__ unsigned char smem_raw[];
-    float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [M][NB]  panel / staged triangle block
-    float2* Us = Ps + (size_t)M * NB;                          // [NB][M]  U12 rows of the current panel
-    float2* drs = Us + (size_t)NB * M;                         // [M]
+    float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [M][PSTR] panel / [M][NB] staged triangle block
+    float2* Us = Ps + (size_t)M * PSTR;                        // [NB][M]  U12 rows; also the 32 x 33 tiles
+    float2* drs = Us + us_len(M);                              // [M]
     float2* invU = drs + M;                                    // [M]
     float* dls = reinterpret_cast<float*>(invU + M);           // [M]
     float* dlb = dls + M;                                      // [M]
@@ -92,6 +95,7 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
     __shared__ double shd[32];
     __shared__ double2 shc[32];
     __shared__ int nswap;
+    __shared__ float2 rowp[NB], rowj[NB];
     const int tid = threadIdx.x;
     const int GT = blockDim.x;
     const int w = blockIdx.x;
@@ -121,13 +125,30 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
     }
     if (tid == 0) nswap = 0;
     __syncthreads();
-    for (long e = tid; e < (long)M * M; e += GT) {
-        int i = (int)(e / M), j = (int)(e % M);
-        double2 t = Tw[e] * ((double)dlb[i] * (double)drb[j]);
-        float2 y = cmul(P.load(Yw, i, j), drs[j]) * dls[i];
-        A[e] = make_float2((float)t.x + y.x, (float)t.y + y.y);
+    {
+        // 32 x 32 tiles: the chain planes are read along i (their contiguous
+        // direction) into shared memory, T^-1 and Mt along j
+        float2* tile = Us;                                       // [32][33] (TILE)
+        const int lane = tid & 31, wid = tid >> 5, nwarp = GT >> 5;
+        for (int ib = 0; ib < M; ib += 32)
+            for (int jb = 0; jb < M; jb += 32) {
+                for (int r = wid; r < 32; r += nwarp) {
+                    const int i = ib + lane, j = jb + r;
+                    tile[r * 33 + lane] = (i < M && j < M) ? P.load(Yw, i, j) : make_float2(0.f, 0.f);
+                }
+                __syncthreads();
+                for (int r = wid; r < 32; r += nwarp) {
+                    const int i = ib + r, j = jb + lane;
+                    if (i < M && j < M) {
+                        const long e = (long)i * M + j;
+                        const double2 t = Tw[e] * ((double)dlb[i] * (double)drb[j]);
+                        const float2 y = cmul(tile[lane * 33 + r], drs[j]) * dls[i];
+                        A[e] = make_float2((float)t.x + y.x, (float)t.y + y.y);
+                    }
+                }
+                __syncthreads();
+            }
     }
-    __syncthreads();
 
     // ---------------------------------------------------------------- blocked LU
     for (int jb = 0; jb < M; jb += NB) {
@@ -135,14 +156,14 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
         const int rows = M - jb;
         for (int e = tid; e < rows * nb; e += GT) {
             const int r = e / nb, c = e % nb;
-            Ps[r * NB + c] = A[(long)(jb + r) * M + jb + c];
+            Ps[r * PSTR + c] = A[(long)(jb + r) * M + jb + c];
         }
         __syncthreads();
         for (int j = 0; j < nb; ++j) {
             float best = -1.0f;
             int bidx = M;
             for (int r = j + tid; r < rows; r += GT) {
-                const float2 v = Ps[r * NB + j];
+                const float2 v = Ps[r * PSTR + j];
                 const float a1 = fabsf(v.x) + fabsf(v.y);
                 if (a1 > best) { best = a1; bidx = r; }
             }
@@ -151,31 +172,36 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
                 p = j;
                 if (tid == 0) atomicOr(status, 1);
             }
-            if (p != j)
-                for (int c = tid; c < nb; c += GT) {
-                    const float2 t = Ps[j * NB + c];
-                    Ps[j * NB + c] = Ps[p * NB + c];
-                    Ps[p * NB + c] = t;
-                }
-            if (tid == 0) piv[jb + j] = jb + p;
+            // stash the pivot row and row j, then update every row from the
+            // stash or from itself: no row is read after another thread wrote it
+            for (int c = tid; c < nb; c += GT) {
+                rowp[c] = Ps[p * PSTR + c];
+                rowj[c] = Ps[j * PSTR + c];
+            }
             __syncthreads();
-            const float2 pv = Ps[j * NB + j];
+            const float2 pv = rowp[j];
             const float n2 = pv.x * pv.x + pv.y * pv.y;
-            if (!(n2 > 0.0f) && tid == 0) atomicOr(status, 1);
             const float2 ip = make_float2(pv.x / n2, -pv.y / n2);
-            if (tid == 0) invU[jb + j] = ip;
-            for (int r = j + 1 + tid; r < rows; r += GT) Ps[r * NB + j] = cmul(Ps[r * NB + j], ip);
-            __syncthreads();
-            const int nr = rows - j - 1, nc = nb - j - 1;
-            for (int e = tid; e < nr * nc; e += GT) {
-                const int r = j + 1 + e / nc, c = j + 1 + e % nc;
-                Ps[r * NB + c] = csub_mul(Ps[r * NB + c], Ps[r * NB + j], Ps[j * NB + c]);
+            if (tid == 0) {
+                if (!(n2 > 0.0f)) atomicOr(status, 1);
+                piv[jb + j] = jb + p;
+                invU[jb + j] = ip;
+            }
+            for (int c = tid; c < nb; c += GT) Ps[j * PSTR + c] = rowp[c];
+            for (int r = j + 1 + tid; r < rows; r += GT) {
+                float2* dst = Ps + r * PSTR;
+                const float2* src = r == p ? rowj : dst;
+                if (r == p)    // the swapped row keeps row j's earlier multipliers
+                    for (int c = 0; c < j; ++c) dst[c] = rowj[c];
+                const float2 l = cmul(src[j], ip);
+                for (int c = j + 1; c < nb; ++c) dst[c] = csub_mul(src[c], l, rowp[c]);
+                dst[j] = l;
             }
             __syncthreads();
         }
         for (int e = tid; e < rows * nb; e += GT) {
             const int r = e / nb, c = e % nb;
-            A[(long)(jb + r) * M + jb + c] = Ps[r * NB + c];
+            A[(long)(jb + r) * M + jb + c] = Ps[r * PSTR + c];
         }
         // the panel's row interchanges on every other column, in order
         for (int c = tid; c < M; c += GT) {
@@ -214,7 +240,7 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
                     float2 s = x[q];
 #pragma unroll
                     for (int q2 = 0; q2 < NB; ++q2)
-                        if (q2 < q) s = csub_mul(s, Ps[q * NB + q2], x[q2]);
+                        if (q2 < q) s = csub_mul(s, Ps[q * PSTR + q2], x[q2]);
                     x[q] = s;
                 }
 #pragma unroll
@@ -245,7 +271,7 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
 #pragma unroll
                     for (int x = 0; x < 4; ++x) {
                         const int r = rg + x * tr;
-                        a[x] = r < nrr ? Ps[(nb + r) * NB + k] : make_float2(0.f, 0.f);
+                        a[x] = r < nrr ? Ps[(nb + r) * PSTR + k] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int y = 0; y < 4; ++y) {
@@ -280,21 +306,24 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
     // ---------------------------------------------------------------- X U = Y D_Rs
     for (int jb = 0; jb < M; jb += NB) {
         const int nb = min(NB, M - jb);
-        for (int e = tid; e < (jb + nb) * nb; e += GT) {
-            const int m = e / nb, q = e % nb;
-            Ps[m * NB + q] = A[(long)m * M + jb + q];
+        for (int e = tid; e < (jb + nb) * NB; e += GT) {   // columns q >= nb zero-filled
+            const int m = e / NB, q = e % NB;
+            Ps[m * NB + q] = q < nb ? A[(long)m * M + jb + q] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         for (int i = tid; i < M; i += GT) {
             float2 s[NB];
 #pragma unroll
             for (int q = 0; q < NB; ++q)
-                if (q < nb) s[q] = cmul(P.load(Yw, i, jb + q), drs[jb + q]);
-            for (int m = 0; m < jb; ++m) {
-                const float2 x = X[(long)i * M + m];
+                s[q] = q < nb ? cmul(P.load(Yw, i, jb + q), drs[jb + q]) : make_float2(0.f, 0.f);
+            for (int m = 0; m < jb; m += 4) {
+                float2 x[4];
 #pragma unroll
-                for (int q = 0; q < NB; ++q)
-                    if (q < nb) s[q] = csub_mul(s[q], x, Ps[m * NB + q]);
+                for (int u = 0; u < 4; ++u) x[u] = X[(long)(m + u) * M + i];
+#pragma unroll
+                for (int q = 0; q < NB; ++q)      // no guard: columns q >= nb are zero
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) s[q] = csub_mul(s[q], x[u], Ps[(m + u) * NB + q]);
             }
 #pragma unroll
             for (int q = 0; q < NB; ++q)
@@ -307,7 +336,7 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
                 }
 #pragma unroll
             for (int q = 0; q < NB; ++q)
-                if (q < nb) X[(long)i * M + jb + q] = s[q];
+                if (q < nb) X[(long)(jb + q) * M + i] = s[q];
         }
         __syncthreads();
     }
@@ -316,21 +345,30 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
     for (int bi = nblk - 1; bi >= 0; --bi) {
         const int jb = bi * NB;
         const int nb = min(NB, M - jb);
-        for (int e = tid; e < (M - jb) * nb; e += GT) {
-            const int m = jb + e / nb, q = e % nb;
-            Ps[(m - jb) * NB + q] = A[(long)m * M + jb + q];
+        for (int e = tid; e < (M - jb) * NB; e += GT) {   // columns q >= nb zero-filled
+            const int m = jb + e / NB, q = e % NB;
+            Ps[(m - jb) * NB + q] = q < nb ? A[(long)m * M + jb + q] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         for (int i = tid; i < M; i += GT) {
             float2 s[NB];
 #pragma unroll
             for (int q = 0; q < NB; ++q)
-                if (q < nb) s[q] = X[(long)i * M + jb + q];
-            for (int m = jb + nb; m < M; ++m) {
-                const float2 x = X[(long)i * M + m];
+                s[q] = q < nb ? X[(long)(jb + q) * M + i] : make_float2(0.f, 0.f);
+            int m = jb + nb;
+            for (; m + 4 <= M; m += 4) {
+                float2 x[4];
 #pragma unroll
-                for (int q = 0; q < NB; ++q)
-                    if (q < nb) s[q] = csub_mul(s[q], x, Ps[(m - jb) * NB + q]);
+                for (int u = 0; u < 4; ++u) x[u] = X[(long)(m + u) * M + i];
+#pragma unroll
+                for (int q = 0; q < NB; ++q)      // no guard: columns q >= nb are zero
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) s[q] = csub_mul(s[q], x[u], Ps[(m + u - jb) * NB + q]);
+            }
+            for (; m < M; ++m) {
+                const float2 x = X[(long)m * M + i];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) s[q] = csub_mul(s[q], x, Ps[(m - jb) * NB + q]);
             }
 #pragma unroll
             for (int q = NB - 2; q >= 0; --q)
@@ -343,17 +381,32 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
                 }
 #pragma unroll
             for (int q = 0; q < NB; ++q)
-                if (q < nb) X[(long)i * M + jb + q] = s[q];
+                if (q < nb) X[(long)(jb + q) * M + i] = s[q];
         }
         __syncthreads();
     }
-    // G[i][perm[m]] = delta - W[i][m] dls[perm[m]]
-    for (int i = tid; i < M; i += GT)
-        for (int m = 0; m < M; ++m) {
-            const int c = perm[m];
-            float2 g = X[(long)i * M + m] * (-dls[c]);
-            if (c == i) g.x += 1.0f;
-            Gw[(long)i * M + c] = g;
+    // G[i][c] = delta_ic - W[i][iperm[c]] dls[c], through 32 x 33 shared tiles
+    // (reads of W columns and writes of G rows both contiguous)
+    for (int m = tid; m < M; m += GT) piv[perm[m]] = m;       // piv <- inverse permutation
+    __syncthreads();
+    float2* tile = Us;                                           // [32][33] (TILE)
+    const int lane = tid & 31, wid = tid >> 5, nwarp = GT >> 5;
+    for (int ib = 0; ib < M; ib += 32)
+        for (int cb = 0; cb < M; cb += 32) {
+            for (int r = wid; r < 32; r += nwarp) {
+                const int c = cb + r, i = ib + lane;
+                tile[r * 33 + lane] = (c < M && i < M) ? X[(long)piv[c] * M + i] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int r = wid; r < 32; r += nwarp) {
+                const int i = ib + r, c = cb + lane;
+                if (i < M && c < M) {
+                    float2 g = tile[lane * 33 + r] * (-dls[c]);
+                    if (c == i) g.x += 1.0f;
+                    Gw[(long)i * M + c] = g;
+                }
+            }
+            __syncthreads();
         }
     __syncthreads();
     double2 trg = make_double2(0.0, 0.0);
@@ -397,7 +450,7 @@ __global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict_
 }  // namespace
 
 size_t green32b_smem(int M) {
-    return (size_t)M * NB * sizeof(float2) * 2 + (size_t)M * (2 * sizeof(float2) + 3 * sizeof(float) + 2 * sizeof(int));
+    return ((size_t)M * PSTR + us_len(M)) * sizeof(float2) + (size_t)M * (2 * sizeof(float2) + 3 * sizeof(float) + 2 * sizeof(int));
 }
 
 cudaError_t launch_green32b(ftq_ctx* c, int k) {
