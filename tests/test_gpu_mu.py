@@ -58,6 +58,43 @@ def test_per_walker_derivatives_match_oracle_fd(ftq):
     assert abs(g["dE"] - ref["dE"]) < 1e-6 * abs(ref["dE"])
 
 
+@pytest.mark.timeout(600)
+def test_mu_tuning_workload_full_size_sampled_walkers(ftq):
+    """The mu-tuning workload at full size (N=14, M=123, r_s=2, Theta=0.25,
+    174 slices, 256 walkers, complex128): every walker's d ln|w|/dmu,
+    dE_L/dmu and dN_L/dmu from the full launch; three sampled walkers checked
+    against the oracle's central differences (h = 1e-4, frozen force bias)."""
+    from oracle_pool import walkers_mu_fd
+    c = WORKLOADS["ueg_n14_m123"]
+    s = UEG(c["N"], c["M"], c["rs"], c["theta"], c["dtau"])
+    W = c["walkers"]
+    f = gaussian_fields(c["seed"], s.n_slices, W, s.N_alpha)
+    p = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W)
+    p.propagate(torch.from_numpy(f).cuda())
+    g = p.mu_grad()
+    pw = g["per_walker"].cpu().numpy()
+    ws = p.weights().cpu().numpy()
+    assert p.status() == 0
+    p.close()
+    alive = [w for w in range(W) if ws[w, 2] > 0.5]
+    assert len(alive) >= W // 2
+    sample = [alive[0], alive[len(alive) // 2], alive[-1]]
+    fd = walkers_mu_fd(system("ueg_n14_m123"), f, sample)
+    checked = 0
+    for w, r in zip(sample, fd):
+        if not r["alive"]:
+            continue
+        checked += 1
+        print(f"walker {w}: dlogw {pw[w, 0]:.10f} / {r['dlogw']:.10f}, dE {pw[w, 2]:.10f} / {r['dE'].real:.10f}, "
+              f"dN {pw[w, 4]:.10f} / {r['dN'].real:.10f}")
+        assert abs(pw[w, 0] - r["dlogw"]) < 1e-6 * max(1, abs(r["dlogw"]))
+        assert abs(pw[w, 2] - r["dE"].real) < 1e-6 * max(1, abs(r["dE"]))
+        assert abs(pw[w, 4] - r["dN"].real) < 1e-6 * max(1, abs(r["dN"]))
+        assert abs(pw[w, 5] - r["dN"].imag) < 1e-6 * max(1, abs(r["dN"]))
+    assert checked >= 2
+    assert math.isfinite(g["dN"]) and math.isfinite(g["dE"])
+
+
 def test_noninteracting_closed_form_full_size(ftq):
     """Zero fields at M=257: the path is free electrons with the propagator's
     energies eps + delta_eps, occupations f, df/dmu = beta f (1 - f):
