@@ -150,6 +150,17 @@ PEAKS = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
 # FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
+# DRAM bytes (read + write) per walker and launch from one ncu capture of the
+# kernel as it stands (files under profiles/); the launches process walkers
+# independently with working sets far above L2, so traffic scales with the
+# walker count.  An entry is removed when its kernel changes.
+TRAFFIC_PER_WALKER = {
+    ("mixed", "qrcp"): (22.672e9 / 128, "profiles/qr_prepiv64_ueg_n66_m257_w128.md"),
+    ("mixed", "green"): (0.863e9 / 128, "profiles/green32b_ueg_n66_m257_w128.md"),
+    ("mixed", "chain"): (0.2455e9 / 128, "profiles/chain_tc_ueg_n66_m257_w128.md"),
+    ("fp64", "chain"): (0.3867e9 / 128, "profiles/chain_fp64_ueg_n66_m257_w128.md"),
+}
+
 
 def kernel_model(kind, M, W, precision):
     """(algorithmic flops of ONE launch, bound, peak TFLOP/s, peak source).
@@ -189,8 +200,14 @@ def roofline(prof, M, W, precision):
                 "traffic": None, "avg_launch_ms": avg_s * 1e3, "share_of_step": share}
     fl, bound, peak, src = model
     ach = fl / avg_s / 1e12
-    return {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": None, "peak_source": src, "avg_launch_ms": avg_s * 1e3, "share_of_step": share}
+    tr = TRAFFIC_PER_WALKER.get((precision, dom))
+    out = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+           "traffic": None if tr is None else tr[0] * W, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
+           "share_of_step": share}
+    if tr is not None:
+        out["traffic_source"] = (f"dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at 128 walkers "
+                                 f"({tr[1]}), scaled to {W} walkers")
+    return out
 
 
 # ---------------------------------------------------------------- ours

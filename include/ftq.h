@@ -61,7 +61,7 @@ typedef struct {
     int      precision;        /* FTQ_FP64, FTQ_MIXED or FTQ_MIXED_SIMT                   */
     int      constraint;       /* FTQ_PHASELESS or FTQ_FREE                               */
     int      reserved;         /* must be 0                                               */
-    uint64_t seed;             /* reserved for the on-device field generator              */
+    uint64_t seed;             /* key of the on-device field generator (ftq_fields)       */
     void*    cuda_stream;      /* cudaStream_t the library launches on (NULL = default)  */
     double   force_bias_cap;   /* 0 = off (no cap is applied in this version)             */
 } ftq_opts;
@@ -88,6 +88,19 @@ typedef struct {
 int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu,
                  double dtau, const ftq_opts* opts);
 
+/* The library's own N(0,1) auxiliary fields (used by ftq_propagate_slices
+ * when fields_dev is NULL): Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+ * with counter (alpha / 2, slice index k (0-based), walker, 0) and key = the
+ * two 32-bit halves (low, high) of opts.seed; the four output words give
+ * u1 = ((w1 << 32 | w0) >> 11 + 1/2) 2^-53 and u2 from (w3, w2) likewise, and
+ * the Box-Muller pair x_alpha = sqrt(-2 ln u1) cos(2 pi u2), x_{alpha+1} =
+ * sqrt(-2 ln u1) sin(2 pi u2) in FP64 (the paper draws x ~ N(0, 1), Sec.
+ * Theory; the generator is this library's choice).
+ *   first_slice, n_slices  window [first_slice, first_slice + n_slices) of [0, n)
+ *   out_dev     caller-owned device float64 [n_slices][W][N_alpha]
+ * FTQ_EINVAL on a window outside [0, n).  Asynchronous on the context stream. */
+int ftq_fields(ftq_ctx* ctx, int first_slice, int n_slices, double* out_dev);
+
 /* Return every walker to tau = 0 (k = 0, unit weights, all alive). */
 int ftq_reset(ftq_ctx* ctx);
 
@@ -98,7 +111,8 @@ int ftq_reset(ftq_ctx* ctx);
  * right block, QRCP every s slices, G(tau_k) and ln det(I + A(tau_k)), and the
  * weight update.
  *   fields_dev  device pointer, float64 [n_slices][W][N_alpha] C order, N(0,1)
- *               draws x_k, caller-owned; must not be NULL in this version.
+ *               draws x_k, caller-owned; or NULL: the library draws them
+ *               itself, slice by slice, with the generator of ftq_fields().
  * The slice counter may not pass n (FTQ_EINVAL).  Asynchronous: numeric
  * breakdown is latched on the device and reported by ftq_status(). */
 int ftq_propagate_slices(ftq_ctx* ctx, int n_slices, const double* fields_dev);
@@ -209,7 +223,8 @@ int ftq_autotune(ftq_ctx* ctx, int* choice, float* ms);
 #define FTQ_K_INIT       5   /* walker initialisation / reset                      */
 #define FTQ_K_BRIDGE     6   /* layout conversions between the FP32 chain and FP64  */
 #define FTQ_K_BORDER     7   /* chain entries outside the tensor-core tile         */
-#define FTQ_K_COUNT      8
+#define FTQ_K_FIELDS     8   /* on-device auxiliary-field generator                */
+#define FTQ_K_COUNT      9
 
 /* Start (enable != 0) or stop per-launch timing.  While on, every kernel
  * launch is bracketed by a CUDA event pair on the context's stream; enabling

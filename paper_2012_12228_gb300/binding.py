@@ -38,11 +38,11 @@ class System(ctypes.Structure):
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
-           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune",
+           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields",
            "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
-           "border": 7}
-K_COUNT = 8
+           "border": 7, "fields": 8}
+K_COUNT = 9
 
 
 def library_path():
@@ -79,6 +79,7 @@ def load_library(path=None):
     lib.ftq_batch_member.argtypes = [vp, i, ctypes.POINTER(vp)]
     lib.ftq_batch_propagate.argtypes = [vp, i, ctypes.POINTER(vp)]
     lib.ftq_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+    lib.ftq_fields.argtypes = [vp, i, i, vp]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]
@@ -179,14 +180,27 @@ class Propagator:
         self._check(self.lib.ftq_reset(self.h), "ftq_reset")
 
     def propagate(self, fields):
-        """fields: CUDA float64 tensor [n][W][N_alpha] (contiguous)."""
+        """fields: CUDA float64 tensor [n][W][N_alpha] (contiguous), or an int n:
+        n slices with the library's own fields (see ``fields``)."""
         t = self._torch
+        if isinstance(fields, int):
+            self._check(self.lib.ftq_propagate_slices(self.h, fields, None), "ftq_propagate_slices")
+            return
         if fields.device.type != "cuda" or fields.dtype != t.float64 or not fields.is_contiguous():
             raise FTQError("fields must be a contiguous CUDA float64 tensor")
         if fields.dim() != 3 or fields.shape[1] != self.W or fields.shape[2] != self.n_alpha:
             raise FTQError(f"fields must have shape [n, {self.W}, {self.n_alpha}]")
         self._check(self.lib.ftq_propagate_slices(self.h, int(fields.shape[0]), ctypes.c_void_p(fields.data_ptr())),
                     "ftq_propagate_slices")
+
+    def fields(self, first_slice, n_slices):
+        """The library's own N(0,1) fields of slices [first_slice, first_slice + n_slices)
+        (Philox4x32-10 keyed by the seed, Box-Muller): CUDA float64 [n][W][N_alpha]."""
+        t = self._torch
+        out = t.empty((n_slices, self.W, self.n_alpha), dtype=t.float64, device="cuda")
+        self._check(self.lib.ftq_fields(self.h, first_slice, n_slices, ctypes.c_void_p(out.data_ptr())),
+                    "ftq_fields")
+        return out
 
     def stabilise(self):
         self._check(self.lib.ftq_stabilise(self.h), "ftq_stabilise")

@@ -42,7 +42,7 @@ void free_all(ftq_ctx* c) {
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
-                    c->tab.hf, c->phi32};
+                    c->tab.hf, c->phi32, c->xbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -181,11 +181,24 @@ int ftq_propagate_slices(ftq_ctx* c, int n_slices, const double* fields_dev) {
     if (n_slices < 0) return fail(c, FTQ_EINVAL, "n_slices must be >= 0");
     if (c->k + n_slices > c->sys.n_slices)
         return fail(c, FTQ_EINVAL, "propagation would pass tau = beta; call ftq_reset first");
-    if (n_slices > 0 && !fields_dev) return fail(c, FTQ_EINVAL, "fields_dev must not be NULL");
     const size_t per_slice = (size_t)c->W * c->sys.n_alpha;
+    if (n_slices > 0 && !fields_dev && !c->xbuf) {
+        cudaError_t e = cudaMalloc(&c->xbuf, per_slice * sizeof(double));
+        if (e != cudaSuccess) {
+            c->xbuf = nullptr;
+            return cuda_fail(c, e, "field buffer");
+        }
+        c->bytes += per_slice * sizeof(double);
+    }
     for (int t = 0; t < n_slices; ++t) {
         const int k = c->k + 1;
-        cudaError_t e = ftq::launch_force_bias(c, fields_dev + per_slice * t);
+        const double* x = fields_dev ? fields_dev + per_slice * t : c->xbuf;
+        cudaError_t e = cudaSuccess;
+        if (!fields_dev) {
+            ftq::LaunchScope ls(c, FTQ_K_FIELDS);
+            e = ftq::launch_philox_fields(c->xbuf, c->opts.seed, 0u, k - 1, 1, c->W, c->sys.n_alpha, c->stream);
+        }
+        if (e == cudaSuccess) e = ftq::launch_force_bias(c, x);
         if (e == cudaSuccess) e = ftq::launch_chain(c);
         if (e == cudaSuccess && c->opts.stabilise_every > 0 && k % c->opts.stabilise_every == 0)
             e = ftq::launch_qrcp(c);
@@ -193,6 +206,18 @@ int ftq_propagate_slices(ftq_ctx* c, int n_slices, const double* fields_dev) {
         if (e != cudaSuccess) return cuda_fail(c, e, "propagate");
         c->k = k;
     }
+    return FTQ_OK;
+}
+
+int ftq_fields(ftq_ctx* c, int first_slice, int n_slices, double* out_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!out_dev) return fail(c, FTQ_EINVAL, "out_dev must not be NULL");
+    if (first_slice < 0 || n_slices < 0 || first_slice + n_slices > c->sys.n_slices)
+        return fail(c, FTQ_EINVAL, "slice window outside [0, n)");
+    ftq::LaunchScope ls(c, FTQ_K_FIELDS);
+    cudaError_t e = ftq::launch_philox_fields(out_dev, c->opts.seed, 0u, first_slice, n_slices, c->W,
+                                              c->sys.n_alpha, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fields");
     return FTQ_OK;
 }
 

@@ -103,6 +103,7 @@ struct ftq_ctx {
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
     bool owns_stream = false;
+    double* xbuf = nullptr;       // one slice of internally drawn fields      [W][N_alpha]
     double2* DR = nullptr;        // D_R                                       [W][M]
     double2* phi = nullptr;       // V generator table per walker              [W][nslot]
     float2* phi32 = nullptr;      // the same table in FP32 (mixed path)       [W][nslot]
@@ -163,6 +164,8 @@ struct LaunchScope {
 // Kernel launchers (fp64_kernels.cu).  All asynchronous on ctx->stream.
 cudaError_t launch_init_walkers(ftq_ctx* c);
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x);
+cudaError_t launch_philox_fields(double* out, uint64_t seed, uint32_t sys, int k0, int n, int W, int na,
+                                 cudaStream_t st);
 cudaError_t launch_chain(ftq_ctx* c);
 cudaError_t launch_qrcp(ftq_ctx* c);
 cudaError_t launch_green(ftq_ctx* c, int k, bool update_weights);
