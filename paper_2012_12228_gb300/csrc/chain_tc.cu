@@ -171,20 +171,28 @@ struct TcBatch {
 };
 
 // Persistent, warp-specialised kernel over a work list of items (system,
-// walker, 64-row block, column tile).
-//   warps 0..7 (256 threads): generate the A tile of every k tile into its
-//       shared-memory stage and arrive on afull[stage]; after an item's last
-//       MMA they run its epilogue (TMEM -> registers -> chain planes).
-//   warp 8, lane 0: waits for A (afull) and B (TMA), issues the 12 MMAs of a
-//       k tile, commits them to mma_bar[stage], and once the previous MMA
-//       group has drained prefetches the next B tile into the freed stage.
-// The stage counter g runs over all k tiles of all items a CTA processes, so
-// mbarrier phases stay consistent across items.  Every wait is bounded; on
-// expiry the kernel latches bit 2 of the status word, drains its own copies
-// and MMAs (bounded) and frees TMEM.
-constexpr int NGEN = 256;                 // generator / epilogue threads
+// walker, 64-row block, column tile), with the accumulator double-buffered in
+// TMEM so that the epilogue of one item overlaps the MMAs of the next.
+//   warps 0..3 (epilogue): wait until item i's accumulator (TMEM buffer i & 1)
+//       is complete, read it lane quadrant by quadrant (warp w owns TMEM lanes
+//       32w..32w+31), add the U term, split to tf32 hi + lo and store the
+//       output planes; then release the buffer.
+//   warps 4..11 (generators): build the A tile of every k tile into its
+//       shared-memory stage and arrive on afull[stage].
+//   warp 12, lane 0 (control): waits for A (afull), B (TMA) and, at the start
+//       of an item, for its TMEM buffer to be released; issues the 12 MMAs of a
+//       k tile, commits them to mma_bar[stage] (and after an item's last k tile
+//       to tfull[buffer]); once the previous MMA group has drained it
+//       prefetches the next B tile into the freed stage.
+// Stage counters run over all k tiles of all items a CTA processes, buffer
+// counters over its items, so mbarrier phases stay consistent.  Every wait is
+// bounded; on expiry the kernel latches bit 2 of the status word, every role
+// skips its remaining work (all warps still pass the same barriers), the
+// control thread drains its own copies and MMAs, and TMEM is freed.
+constexpr int NEPI = 128;                 // epilogue threads (4 warps)
+constexpr int NGEN = 256;                 // generator threads (8 warps)
 constexpr int NCTRL = 32;                 // control warp
-constexpr int NTHREADS_WS = NGEN + NCTRL;
+constexpr int NTHREADS_WS = NEPI + NGEN + NCTRL;
 
 __device__ __forceinline__ void gen_barrier() {
     asm volatile("bar.sync 1, %0;" ::"n"(NGEN) : "memory");
@@ -213,7 +221,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_constant__ TcBatch tb,
                                                              const int4* __restrict__ items, int nitems) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t tma_bar[2], mma_bar[2], afull[2];
+    __shared__ uint64_t tma_bar[2], mma_bar[2], afull[2], tfull[2], tempty[2];
     __shared__ uint32_t tmem_sh;
     __shared__ volatile int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -225,26 +233,28 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
     float2* phs = reinterpret_cast<float2*>(base + 2 * stage_bytes);
     int* pks = reinterpret_cast<int*>(phs + tb.nslot_max);
     uint16_t* qs = reinterpret_cast<uint16_t*>(pks + tb.m_max);
+    int* st = tb.args[0].status;
 
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tma_bar[b], 1);
             mbar_init(&mma_bar[b], 1);
             mbar_init(&afull[b], NGEN / 32);
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], NEPI / 32);
         }
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(&tmem_sh, (uint32_t)tb.ncols);
+    if (warp == 0) tmem_alloc(&tmem_sh, 2u * (uint32_t)tb.ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_sh;
 
-    if (warp == NGEN / 32) {
+    if (warp == (NEPI + NGEN) / 32) {
         // ------------------------------------------------ control warp
         if (lane == 0) {
-            int* st = tb.args[0].status;
             int g = 0, last_tma = -1, last_mma = -1;
             auto issue_tma = [&](int4 it, int kt, int gi) {
                 const TcArgs& q = tb.args[it.x];
@@ -258,11 +268,16 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
             };
             bool ok = true;
             if ((int)blockIdx.x < nitems) issue_tma(items[blockIdx.x], 0, 0);
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            int li = 0;                                   // items of this CTA so far
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
                 const int4 it = items[item];
                 const int4 nx = item + (int)gridDim.x < nitems ? items[item + gridDim.x] : make_int4(0, 0, 0, 0);
                 const TcArgs& p = tb.args[it.x];
                 const uint32_t idesc = idesc_tf32(p.NT);
+                const int tb_i = li & 1;
+                const uint32_t acc = tmem + (uint32_t)(tb_i * tb.ncols);
+                // the epilogue of item li - 2 must have released this buffer
+                if (li >= 2) ok = mbar_wait_ab(&tempty[tb_i], (uint32_t)(((li - 2) >> 1) & 1), &abort_sh, st);
                 for (int kt = 0; kt < p.ktiles && ok; ++kt, ++g) {
                     const int s = g & 1, use = g >> 1;
                     ok = mbar_wait_ab(&afull[s], (uint32_t)(use & 1), &abort_sh, st) &&
@@ -275,11 +290,12 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
 #pragma unroll
                     for (int k = 0; k < KTILE / 8; ++k) {
                         const uint64_t dk = (uint64_t)((k * 32) >> 4);   // 8 tf32 = 32 bytes along the row
-                        mma_tf32(tmem, ah + dk, bh + dk, idesc, (kt > 0 || k > 0) ? 1u : 0u);
-                        mma_tf32(tmem, ah + dk, bl + dk, idesc, 1u);
-                        mma_tf32(tmem, al + dk, bh + dk, idesc, 1u);
+                        mma_tf32(acc, ah + dk, bh + dk, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                        mma_tf32(acc, ah + dk, bl + dk, idesc, 1u);
+                        mma_tf32(acc, al + dk, bh + dk, idesc, 1u);
                     }
                     mma_commit(&mma_bar[s]);
+                    if (kt + 1 == p.ktiles) mma_commit(&tfull[tb_i]);   // accumulator complete
                     last_mma = g;
                     // MMA(g - 1) frees stage s ^ 1 for the next B tile
                     if (g >= 1) ok = mbar_wait_ab(&mma_bar[s ^ 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st);
@@ -293,31 +309,32 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                 if (last_mma >= 0) mbar_wait(&mma_bar[last_mma & 1], (uint32_t)((last_mma >> 1) & 1));
             }
         }
-    } else {
-        // ------------------------------------------------ generator / epilogue warps
-        // After an abort every generator warp still passes the same named
-        // barriers (loop bounds are uniform); only the work is skipped.
-        int* st = tb.args[0].status;
+    } else if (warp >= NEPI / 32) {
+        // ------------------------------------------------ generator warps
+        // Loop bounds are uniform over these warps, so after an abort they
+        // still pass the same named barriers; only the work is skipped.
+        const int gw = warp - NEPI / 32, gt = tid - NEPI;
         int g = 0;
         int loaded_sys = -1;
-        // swizzled offsets: row j = warp + 8 t has (j & 7) = warp and (j >> 3) = t
-        const uint32_t off_top = (uint32_t)(warp * 128 + ((((lane >> 2) ^ warp) & 7) << 4) + (lane & 3) * 4);
+        // swizzled offsets: row j = gw + 8 t has (j & 7) = gw and (j >> 3) = t
+        const uint32_t off_top = (uint32_t)(gw * 128 + ((((lane >> 2) ^ gw) & 7) << 4) + (lane & 3) * 4);
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             const int4 it = items[item];
             const TcArgs& p = tb.args[it.x];
-            const int w = it.y, rows0 = it.z * 64, col0 = it.w * p.NT;
+            const int w = it.y, rows0 = it.z * 64;
             const float2* ph = p.phi + (long)w * p.nslot;
-            for (int i = tid; i < p.nslot; i += NGEN) phs[i] = ph[i];
+            gen_barrier();        // every generator is done with the previous item's tables
+            for (int i = gt; i < p.nslot; i += NGEN) phs[i] = ph[i];
             if (it.x != loaded_sys) {
-                for (int i = tid; i < p.M; i += NGEN) pks[i] = p.pk[i];
-                for (int i = tid; i < p.qsize; i += NGEN) qs[i] = p.qcube[i];
+                for (int i = gt; i < p.M; i += NGEN) pks[i] = p.pk[i];
+                for (int i = gt; i < p.qsize; i += NGEN) qs[i] = p.qcube[i];
                 loaded_sys = it.x;
             }
             gen_barrier();
             int prow[64 / (NGEN / 32)];
 #pragma unroll
             for (int t = 0; t < 64 / (NGEN / 32); ++t) {
-                const int i = rows0 + warp + t * (NGEN / 32);
+                const int i = rows0 + gw + t * (NGEN / 32);
                 prow[t] = i < p.M ? pks[i] + p.qoff : -1;
             }
             for (int kt = 0; kt < p.ktiles; ++kt, ++g) {
@@ -343,7 +360,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                     const float bot = im_half ? v.x : v.y;
                     float h, l;
                     split_tf32(top, h, l);
-                    uint32_t o = off_top + (uint32_t)t * 1024u;          // element (warp + 8 t, lane)
+                    uint32_t o = off_top + (uint32_t)t * 1024u;          // element (gw + 8 t, lane)
                     *reinterpret_cast<float*>(Ahi + o) = h;
                     *reinterpret_cast<float*>(Alo + o) = l;
                     split_tf32(bot, h, l);
@@ -355,10 +372,18 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&afull[s]);
             }
-            // the item's accumulator: wait for its last MMA group
-            const bool acc_ok = mbar_wait_ab(&mma_bar[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st);
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        int li = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
+            const int4 it = items[item];
+            const TcArgs& p = tb.args[it.x];
+            const int tb_i = li & 1;
+            const bool acc_ok = mbar_wait_ab(&tfull[tb_i], (uint32_t)((li >> 1) & 1), &abort_sh, st);
             tc_fence_after();
-            const int r = (warp & 3) * 32 + lane;        // accumulator row = TMEM lane
+            const int w = it.y, rows0 = it.z * 64, col0 = it.w * p.NT;
+            const int r = warp * 32 + lane;               // accumulator row = TMEM lane
             const int i = rows0 + (r & 63);
             const int part = r >> 6;                      // 0: Re C, 1: Im C
             const bool row_ok = i < p.M;
@@ -370,40 +395,59 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
             const float* __restrict__ U = p.Yu + wstride * w;
             float* __restrict__ O = p.out + wstride * w;
             const int cend = min(col0 + p.NT, p.M);
-            for (int ch = warp >> 2; acc_ok && ch * 16 < p.NT; ch += 2) {
-                uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ch * 16), v);
-                if (row_ok) {
-                    float uh[16], ul[16];
+            const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tb_i * tb.ncols);
+            const int nch = (p.NT + 15) / 16;
+            // U of chunk ch + 1 is loaded while chunk ch is finished, so that two
+            // chunks of loads are in flight per thread
+            float uh[2][16], ul[2][16];
+            auto load_u = [&](int ch, float (&h)[16], float (&l)[16]) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {        // all loads first, then all stores
-                        const int c = col0 + ch * 16 + q;
+                for (int q = 0; q < 16; ++q) {
+                    const int c = col0 + ch * 16 + q;
+                    const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
+                    const bool ok = row_ok && c < cend;
+                    h[q] = ok ? U[o] : 0.f;
+                    l[q] = ok ? U[partoff + o] : 0.f;
+                }
+            };
+            auto finish = [&](int ch, const uint32_t (&v)[16], const float (&h)[16], const float (&l)[16]) {
+                if (!row_ok) return;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = col0 + ch * 16 + q;
+                    if (c < cend) {
                         const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
-                        uh[q] = c < cend ? U[o] : 0.f;
-                        ul[q] = c < cend ? U[partoff + o] : 0.f;
+                        const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(h[q] + l[q])));
+                        float hh, ll;
+                        split_tf32(val, hh, ll);
+                        O[o] = hh;
+                        O[partoff + o] = ll;
                     }
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int c = col0 + ch * 16 + q;
-                        if (c < cend) {
-                            const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
-                            const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(uh[q] + ul[q])));
-                            float h, l;
-                            split_tf32(val, h, l);
-                            O[o] = h;
-                            O[partoff + o] = l;
-                        }
+                }
+            };
+            if (acc_ok) {
+                load_u(0, uh[0], ul[0]);
+                for (int ch = 0; ch < nch; ch += 2) {
+                    uint32_t v[16];
+                    tmem_ld16(acc + (uint32_t)(ch * 16), v);
+                    if (ch + 1 < nch) load_u(ch + 1, uh[1], ul[1]);
+                    finish(ch, v, uh[0], ul[0]);
+                    if (ch + 1 < nch) {
+                        tmem_ld16(acc + (uint32_t)((ch + 1) * 16), v);
+                        if (ch + 2 < nch) load_u(ch + 2, uh[0], ul[0]);
+                        finish(ch + 1, v, uh[1], ul[1]);
                     }
                 }
             }
             tc_fence_before();
-            gen_barrier();        // all accumulator reads and generation done before the next item
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[tb_i]);    // this warp's quadrant is read
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, (uint32_t)tb.ncols);
+    if (warp == 0) tmem_dealloc(tmem, 2u * (uint32_t)tb.ncols);
 }
 
 // Output entries outside the MMA tile: rows [R, M) x all columns and
@@ -608,6 +652,7 @@ cudaError_t launch_items(ftq_ctx* timing_ctx, const TcBatch& tb, const int4* ite
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_tc, NTHREADS_WS, smem);
+    per_sm = std::min(per_sm, 512 / (2 * tb.ncols));   // two accumulators per CTA in 512 TMEM columns
     if (per_sm < 1) per_sm = 1;
     const int grid = std::min(nitems, sms * per_sm);
     LaunchScope ls(timing_ctx, FTQ_K_CHAIN);
