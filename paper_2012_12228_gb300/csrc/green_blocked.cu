@@ -4,16 +4,19 @@
 // organised so that almost all flops are register-tiled updates from
 // shared memory instead of streams through L2:
 //
-//   LU: 32-column panels factorised in shared memory; the row swaps are
+//   LU: NB-column panels factorised in shared memory; the row swaps are
 //       applied to the rest of the matrix column by column; U12 = L11^-1 A12
 //       one column per thread; A22 -= L21 U12 in 4 x 4 complex micro-tiles.
-//   X U = Y D_Rs and W L = X: 32-column blocks, one row per thread, the
+//   X U = Y D_Rs and W L = X: NB-column blocks, one row per thread, the
 //       block of U (or L) staged in shared memory and broadcast; X is stored
 //       column-major so that a warp's loads of one column are contiguous.
 //   G is written through 32 x 33 shared tiles with the inverse pivot order.
 //
-// One thread block per walker (ceil(M/32) warps, 256..384 threads, so that
-// the solves take one row per thread); matrices live in L2 / HBM.
+// One thread block per walker (ceil(M/32) warps, 256..288 threads, so that
+// the solves take one row per thread); matrices live in L2 / HBM.  The kernel
+// is latency-bound, so the panel width (NB = 8) and the register cap are
+// chosen for occupancy: four walkers per SM (a measured sweep over NB = 4, 8,
+// 16, 32 and one to five blocks per SM at M = 257).
 #include <cmath>
 
 #include "complex_math.cuh"
@@ -23,13 +26,13 @@
 namespace ftq {
 namespace {
 
-constexpr int NB = 32;
+constexpr int NB = 8;
 constexpr int PSTR = NB + 1;   // padded row stride of the LU panel (column reads conflict-free)
 constexpr int TILE = 32 * 33;  // one padded 32 x 32 transpose tile
 
 // Length of the U12 region, which also holds the transpose tile.
 __host__ __device__ __forceinline__ int us_len(int M) { return NB * M > TILE ? NB * M : TILE; }
-constexpr int GT_MAX = 384;
+constexpr int GT_MAX = 288;
 constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ float2 csub_mul(float2 acc, float2 a, float2 b) {
@@ -74,7 +77,7 @@ __device__ int bargmax(float val, int idx, float* shv, int* shi) {
     return bi;
 }
 
-__global__ void __launch_bounds__(GT_MAX, 1) k_green32b(const float* __restrict__ Ypl, const double2* __restrict__ Tinv,
+__global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict__ Ypl, const double2* __restrict__ Tinv,
                                                    const double2* __restrict__ DR, float2* __restrict__ work,
                                                    float2* __restrict__ work2, float2* __restrict__ G,
                                                    const double* __restrict__ eps, double* __restrict__ ws,
