@@ -41,7 +41,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
@@ -405,7 +405,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "N": c["N"], "M": head["M"], "rs": c["rs"], "theta": c["theta"],
                    "dtau": head["dtau"], "n_slices": head["n_slices"], "walkers": W,
                    "slices_per_step": head["stab"], "exp_order": head["p"], "precision": args.precision,
-                   "step": "one stabilisation block (5 slices) for all walkers; one estimator call per timed run",
+                   "step": "one stabilisation block (5 slices) for all walkers; one estimator call per timed run "
+                           "(the path evaluates the estimators once, at tau = beta, every 348 slices)",
                    "l2": "inputs larger than L2: walker state > 7 GB per rank",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": head["roofline"],
