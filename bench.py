@@ -155,7 +155,6 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # independently with working sets far above L2, so traffic scales with the
 # walker count.  An entry is removed when its kernel changes.
 TRAFFIC_PER_WALKER = {
-    ("mixed", "qrcp"): (23.483e9 / 128, "profiles/qr_prepiv64_ueg_n66_m257_w128.md"),
     ("mixed", "green"): (1.054e9 / 128, "profiles/green32b_ueg_n66_m257_w128.md"),
     ("mixed", "chain"): (0.2438e9 / 128, "profiles/chain_tc_ueg_n66_m257_w128.md"),
     ("fp64", "chain"): (0.3867e9 / 128, "profiles/chain_fp64_ueg_n66_m257_w128.md"),

@@ -42,7 +42,7 @@ void free_all(ftq_ctx* c) {
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
-                    c->tab.hf, c->phi32, c->xbuf};
+                    c->tab.hf, c->phi32, c->xbuf, c->xsum};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -100,6 +100,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         chk(dalloc(c, &c->G32, W * MM));
         chk(dalloc(c, &c->w32, W * MM));
         chk(dalloc(c, &c->w2_32, W * MM));
+        chk(dalloc(c, &c->xsum, W * MM));
     }
     chk(dalloc(c, &c->Tinv, W * MM));
     chk(dalloc(c, &c->G, W * MM));

@@ -109,6 +109,7 @@ struct ftq_ctx {
     float2* phi32 = nullptr;      // the same table in FP32 (mixed path)       [W][nslot]
     double2* hh = nullptr;        // Householder u_0 per column                [W][M]
     double* htau = nullptr;       // Householder tau                           [W][M]
+    double* xsum = nullptr;       // Re + Im of the T^-1 update's X (mixed)    [W][M][M]
     int* perm = nullptr;          // pivot permutation scratch                 [W][M]
     double* wstate = nullptr;     // [W][WSTRIDE] per-walker state (layout above)
     double* est = nullptr;        // [W][WSTRIDE] per-walker estimators

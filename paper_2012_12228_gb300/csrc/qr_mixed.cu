@@ -46,7 +46,8 @@ __device__ double bsum_d(double v, double* sh) {
 // uncapped blocks or smaller blocks at M = 257)
 __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict__ Ypl, double2* __restrict__ work,
                               double2* __restrict__ work2, double2* __restrict__ DR, double2* __restrict__ Tinv,
-                              float2* __restrict__ VT, double* __restrict__ htau, double* __restrict__ ws,
+                              float2* __restrict__ VT, double* __restrict__ htau, double* __restrict__ xsum,
+                              double* __restrict__ ws,
                               int* __restrict__ status, int M, Planes P, size_t wstride) {
     extern __shared__ unsigned char smem_raw[];
     double* cn = reinterpret_cast<double*>(smem_raw);      // [M] column norms of C
@@ -143,12 +144,36 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
         if (c > i) C[e] = cdiv(C[e], C[(long)i * M + i]);
     }
     __syncthreads();
-    // T^-1 <- T^-1[:, perm] U^-1, one row per thread (XT column-major)
+    // Re U + Im U of the strict upper triangle, kept in the real parts of the
+    // (no longer needed) lower triangle: U[m][j] -> C[j][m].x
+    for (long e = tid; e < (long)M * M; e += nt) {
+        const int j = (int)(e / M), m = (int)(e % M);
+        if (m < j) {
+            const double2 u = C[(long)m * M + j];
+            C[e].x = u.x + u.y;
+        }
+    }
+    __syncthreads();
+    // T^-1 <- T^-1[:, perm] U^-1, one row per thread (XT column-major).  The
+    // complex sums over m use three real products per term (sum ac, sum bd,
+    // sum (a + b)(c + d): the three-multiplication complex product), with
+    // a + b of X kept beside X and c + d of U precomputed above.
+    double* XS = xsum + off;
     for (int i = tid; i < M; i += nt) {
         for (int j = 0; j < M; ++j) {
+            double pr = 0.0, qr = 0.0, rr = 0.0;
+            for (int m = 0; m < j; ++m) {
+                const double2 x = XT[(long)m * M + i];
+                const double2 u = C[(long)m * M + j];
+                pr = fma(x.x, u.x, pr);
+                qr = fma(x.y, u.y, qr);
+                rr = fma(XS[(long)m * M + i], C[(long)j * M + m].x, rr);
+            }
             double2 s = Ti[(long)i * M + perm[j]];
-            for (int m = 0; m < j; ++m) s = cfms(XT[(long)m * M + i], C[(long)m * M + j], s);
+            s.x -= pr - qr;
+            s.y -= rr - pr - qr;
             XT[(long)j * M + i] = s;
+            XS[(long)j * M + i] = s.x + s.y;
         }
         for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
     }
@@ -234,7 +259,7 @@ cudaError_t launch_qr_prepiv(ftq_ctx* c) {
     {
         LaunchScope ls(c, FTQ_K_QRCP);
         k_qr_prepiv64<<<c->W, nt, sm1, c->stream>>>(c->Ypl, c->work, c->work2, c->DR, c->Tinv, c->w2_32, c->htau,
-                                                    c->wstate, c->status, M, P, ws);
+                                                    c->xsum, c->wstate, c->status, M, P, ws);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
