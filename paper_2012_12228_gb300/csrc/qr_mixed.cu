@@ -44,6 +44,38 @@ __device__ double bsum_d(double v, double* sh) {
 
 // (launch bounds: four 288-thread blocks per SM; measured faster than three
 // uncapped blocks or smaller blocks at M = 257)
+// Block sum of a complex value; every thread returns the total.
+__device__ double2 bsum_c(double2 v, double2* sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double2 acc = sh[0];
+    for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i) acc = acc + sh[i];
+    __syncthreads();
+    return acc;
+}
+
+// Householder reflector of column j from its squared norm s (rows >= j):
+// beta = -|x| x_j/|x_j| replaces C[j][j]; u_j = x_j - beta, tau = 2/(u^H u).
+__device__ void reflector_head(double2* C, double* htau_w, int* status, int M, int j, double s, double2* u0,
+                               double* tau) {
+    const double2 al = C[(long)j * M + j];
+    const double sig = sqrt(s);
+    const double aa = sqrt(abs2(al));
+    const double2 beta = aa > 0.0 ? al * (-sig / aa) : make_double2(-sig, 0.0);
+    const double uhu = 2.0 * sig * (sig + aa);
+    *u0 = al - beta;
+    *tau = uhu > 0.0 ? 2.0 / uhu : 0.0;
+    htau_w[j] = *tau;
+    C[(long)j * M + j] = beta;
+    if (!(sig > 0.0)) atomicOr(status, 1);
+}
+
 __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict__ Ypl, double2* __restrict__ work,
                               double2* __restrict__ work2, double2* __restrict__ DR, double2* __restrict__ Tinv,
                               float2* __restrict__ VT, double* __restrict__ htau, double* __restrict__ xsum,
@@ -54,8 +86,8 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
     int* perm = reinterpret_cast<int*>(cn + M);            // [M] C Pi column j = C column perm[j]
     unsigned char* seen = reinterpret_cast<unsigned char*>(perm + M);   // [M]
     __shared__ double shd[32];
-    __shared__ double2 piv_u0;
-    __shared__ double piv_tau;
+    __shared__ double2 piv_u0, piv_u1, shc2[32];
+    __shared__ double piv_tau, piv_tau1;
     __shared__ int parity;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int w = blockIdx.x;
@@ -104,36 +136,76 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
     }
     __syncthreads();
 
-    for (int j = 0; j < M; ++j) {
+    // Householder QR of C Pi, two reflectors per pass over the trailing
+    // columns: H_j is applied to column j + 1 first and u_{j+1} formed; then
+    // every later column x takes both in one read pass (d1 = u_j^H x,
+    // d2 = u_{j+1}^H x) and one write pass, x -= a1 u_j + a2 u_{j+1} with
+    // a1 = tau_j d1 and a2 = tau_{j+1} (d2 - a1 u_{j+1}^H u_j).
+    for (int j = 0; j < M; j += 2) {
         double s = 0.0;
         for (int r = j + tid; r < M; r += nt) s += abs2(C[(long)r * M + j]);
         s = bsum_d(s, shd);
-        if (tid == 0) {
-            const double2 al = C[(long)j * M + j];
-            const double sig = sqrt(s);
-            const double aa = sqrt(abs2(al));
-            const double2 beta = aa > 0.0 ? al * (-sig / aa) : make_double2(-sig, 0.0);
-            const double uhu = 2.0 * sig * (sig + aa);
-            piv_u0 = al - beta;
-            piv_tau = uhu > 0.0 ? 2.0 / uhu : 0.0;
-            htau[(long)w * M + j] = piv_tau;
-            C[(long)j * M + j] = beta;
-            if (!(sig > 0.0)) atomicOr(status, 1);
-        }
+        if (tid == 0) reflector_head(C, htau + (long)w * M, status, M, j, s, &piv_u0, &piv_tau);
         __syncthreads();
-        const double2 uj = piv_u0;
+        const double2 uj = piv_u0;           // u_j[j]; u_j[r] = C[r][j] below
         const double tj = piv_tau;
         // reflector j in FP32 for the Q panels: V[j][r] = u_r, r >= j
         for (int r = j + tid; r < M; r += nt) {
             const double2 u = r == j ? uj : C[(long)r * M + j];
             V[(long)j * M + r] = make_float2((float)u.x, (float)u.y);
         }
-        for (int c = j + 1 + tid; c < M; c += nt) {
-            double2 acc = cmul(conj(uj), C[(long)j * M + c]);
-            for (int r = j + 1; r < M; ++r) acc = cfma(conj(C[(long)r * M + j]), C[(long)r * M + c], acc);
-            acc = acc * tj;
-            C[(long)j * M + c] = cfms(uj, acc, C[(long)j * M + c]);
-            for (int r = j + 1; r < M; ++r) C[(long)r * M + c] = cfms(C[(long)r * M + j], acc, C[(long)r * M + c]);
+        if (j + 1 >= M) break;
+        // H_j on column j + 1
+        double2 d = make_double2(0.0, 0.0);
+        for (int r = j + tid; r < M; r += nt) {
+            const double2 u = r == j ? uj : C[(long)r * M + j];
+            d = cfma(conj(u), C[(long)r * M + j + 1], d);
+        }
+        const double2 a = bsum_c(d, shc2) * tj;
+        for (int r = j + tid; r < M; r += nt) {
+            const double2 u = r == j ? uj : C[(long)r * M + j];
+            C[(long)r * M + j + 1] = cfms(u, a, C[(long)r * M + j + 1]);
+        }
+        __syncthreads();
+        // reflector j + 1
+        s = 0.0;
+        for (int r = j + 1 + tid; r < M; r += nt) s += abs2(C[(long)r * M + j + 1]);
+        s = bsum_d(s, shd);
+        if (tid == 0) reflector_head(C, htau + (long)w * M, status, M, j + 1, s, &piv_u1, &piv_tau1);
+        __syncthreads();
+        const double2 u1 = piv_u1;           // u_{j+1}[j+1]; u_{j+1}[r] = C[r][j+1] below
+        const double t1 = piv_tau1;
+        for (int r = j + 1 + tid; r < M; r += nt) {
+            const double2 u = r == j + 1 ? u1 : C[(long)r * M + j + 1];
+            V[(long)(j + 1) * M + r] = make_float2((float)u.x, (float)u.y);
+        }
+        // g = u_{j+1}^H u_j (rows >= j + 1)
+        double2 gp = make_double2(0.0, 0.0);
+        for (int r = j + 1 + tid; r < M; r += nt) {
+            const double2 u = r == j + 1 ? u1 : C[(long)r * M + j + 1];
+            gp = cfma(conj(u), C[(long)r * M + j], gp);
+        }
+        const double2 g = bsum_c(gp, shc2);
+        const double2 uj1 = C[(long)(j + 1) * M + j];    // u_j[j+1]
+        for (int c = j + 2 + tid; c < M; c += nt) {
+            const double2 x0 = C[(long)j * M + c], x1 = C[(long)(j + 1) * M + c];
+            double2 d1 = cfma(conj(uj1), x1, cmul(conj(uj), x0));
+            double2 d2 = cmul(conj(u1), x1);
+            for (int r = j + 2; r < M; ++r) {
+                const double2 x = C[(long)r * M + c];
+                d1 = cfma(conj(C[(long)r * M + j]), x, d1);
+                d2 = cfma(conj(C[(long)r * M + j + 1]), x, d2);
+            }
+            const double2 a1 = d1 * tj;
+            const double2 a2 = cfms(a1, g, d2) * t1;
+            C[(long)j * M + c] = cfms(uj, a1, x0);
+            C[(long)(j + 1) * M + c] = cfms(u1, a2, cfms(uj1, a1, x1));
+            for (int r = j + 2; r < M; ++r) {
+                double2 x = C[(long)r * M + c];
+                x = cfms(C[(long)r * M + j], a1, x);
+                x = cfms(C[(long)r * M + j + 1], a2, x);
+                C[(long)r * M + c] = x;
+            }
         }
         __syncthreads();
     }
