@@ -18,6 +18,8 @@ ed       exact diagonalisation of the grand-canonical ensemble (M <= 7).
 afqmc    walker propagation: force bias, V(x), Taylor exp, B chain, QRCP
          stabilisation, stable Green's function, phaseless / free-projection
          weights, energy and particle-number estimators.
+population  comb population control between slices (the method the paper
+         names in its Computational Details), with the draw passed in.
 
 Every function cites the section / equation of the paper it follows.  Where
 the paper is silent, garbled or self-contradictory the reading taken is
