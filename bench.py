@@ -296,8 +296,39 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     out["kernel_ms_per_step"] = {k: v["ms"] for k, v in prof.items() if v["ms"] > 0}
     out["roofline"] = roofline(prof, M, W, precision)
     out["device_status"] = prop.status()
+    out["population_control"] = measure_comb(torch, prop, stream, precision, fields)
     prop.close()
     return out
+
+
+def measure_comb(torch, prop, stream, precision, fields):
+    """Comb population control of all walkers (after the measured blocks; one
+    untimed block of 5 slices before each comb so that the weights differ):
+    ms per comb and the achieved copy bandwidth (each copied walker's state
+    is read once and written once)."""
+    M, W = prop.M, prop.W
+    Kp, LD = (M + 15) // 16 * 16, (M + 7) // 8 * 8
+    walker_bytes = (16 * M * M + 16 * M * M + 16 * M + 8 * 16 +
+                    (16 * M * M if precision == "fp64" else 8 * LD * 2 * Kp + 8 * M * M))
+    draws = [0.37, 0.71]
+    ms, moved = 0.0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ident = torch.arange(W, device="cuda", dtype=torch.int32)
+    for i, x in enumerate(draws):
+        prop.propagate(fields[2 + i])
+        torch.cuda.synchronize()
+        e0.record(stream)
+        par = prop.population_control(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        moved += int((par != ident).sum().item())
+    ms /= len(draws)
+    gbs = 2.0 * walker_bytes * moved / len(draws) / (ms / 1e3) / 1e9
+    return {"ms_per_comb": ms, "walkers_copied_per_comb": moved / len(draws), "bytes_per_walker": walker_bytes,
+            "copy_GBps": gbs, "hbm_frac": gbs / PEAKS.get("hbm_gbs", 6800.0),
+            "note": "comb of all walkers after the measured blocks (not part of the timed step); "
+                    "hbm_frac of the measured copy bandwidth"}
 
 
 def measure_ragged(ftq, torch, dev, steps=4, warmup=3):
@@ -417,6 +448,7 @@ def run_ours(args, rank, world, local_rank):
         "kernel_ms_per_step": head["kernel_ms_per_step"],
         "estimate": head["estimate"],
         "device_status": head["device_status"],
+        "population_control": head["population_control"],
     }
     if comparison:
         line["fp64_path"] = {"value": comparison["value"], "ms_per_step": comparison["ms_per_step"],

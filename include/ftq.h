@@ -101,6 +101,26 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
  * FTQ_EINVAL on a window outside [0, n).  Asynchronous on the context stream. */
 int ftq_fields(ftq_ctx* ctx, int first_slice, int n_slices, double* out_dev);
 
+/* Comb population control between slices (Computational Details: the comb
+ * method).  With the phaseless weights w_i = exp(ln|w_i| - max ln|w|) of the
+ * alive walkers (dead walkers weigh 0) and their running sums C_i in index
+ * order (FP64), W teeth t_k = (k + xi) (S / W), S = C_{W-1}, are placed; walker
+ * i receives the teeth in [C_{i-1}, C_i) (the last walker the rest), i.e. n_i
+ * copies.  Walkers with n_i >= 1 keep their slot; their extra copies fill the
+ * slots of walkers with n_i = 0 (sources and slots each in ascending order),
+ * by copying the whole walker state (chain, T^-1, D_R, G, ln det, weight
+ * record).  Afterwards every walker is alive with ln|w| = ln(S / W) + max and
+ * phase 0.
+ *   xi          the comb's uniform draw in [0, 1), supplied by the caller
+ *   parent_dev  nullable device int32 [W]: the walker each slot was copied from
+ *               (itself for survivors)
+ * FTQ_EINVAL for xi outside [0, 1), free-projection contexts, batch handles
+ * (comb each member) and W > 65535.  A comb with no walker alive changes
+ * nothing and latches FTQ_ENUMERIC.  After a comb, ftq_mu_grad is refused
+ * until ftq_reset (the derivative at fixed draws does not extend across the
+ * resampling).  Asynchronous on the context stream. */
+int ftq_population_control(ftq_ctx* ctx, double xi, int* parent_dev);
+
 /* Return every walker to tau = 0 (k = 0, unit weights, all alive). */
 int ftq_reset(ftq_ctx* ctx);
 
@@ -224,7 +244,8 @@ int ftq_autotune(ftq_ctx* ctx, int* choice, float* ms);
 #define FTQ_K_BRIDGE     6   /* layout conversions between the FP32 chain and FP64  */
 #define FTQ_K_BORDER     7   /* chain entries outside the tensor-core tile         */
 #define FTQ_K_FIELDS     8   /* on-device auxiliary-field generator                */
-#define FTQ_K_COUNT      9
+#define FTQ_K_POPULATION 9   /* comb population control                            */
+#define FTQ_K_COUNT      10
 
 /* Start (enable != 0) or stop per-launch timing.  While on, every kernel
  * launch is bracketed by a CUDA event pair on the context's stream; enabling

@@ -5,7 +5,7 @@ The paper controls the walker population with the comb method (Computational
 Details; Booth, Thom and Alavi 2009, and the CPMC-Lab description) and names
 pair branching for low temperatures without giving either algorithm.  The
 comb, from its published definition: with phaseless weights w_i (i < W) and
-their running sums C_i, put W teeth at t_k = (k + xi) S / W (k < W,
+their running sums C_i, put W teeth at t_k = (k + xi) (S / W) (k < W,
 S = C_{W-1}, one uniform draw xi in [0, 1)); walker i receives the teeth in
 [C_{i-1}, C_i), i.e. n_i copies, and every copy carries the weight S / W.
 
@@ -28,11 +28,11 @@ def comb_counts(weights, xi):
     w = np.asarray(weights, dtype=np.float64)
     W = len(w)
     C = np.cumsum(w)                     # running sums, sequential in index order
-    S = C[-1]
+    step = C[-1] / W
     n = np.zeros(W, dtype=np.int64)
     i = 0
     for k in range(W):
-        t = (k + xi) * S / W
+        t = (k + xi) * step
         while i < W - 1 and t >= C[i]:
             i += 1
         n[i] += 1

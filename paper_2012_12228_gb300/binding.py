@@ -38,11 +38,11 @@ class System(ctypes.Structure):
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
-           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields",
+           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control",
            "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
-           "border": 7, "fields": 8}
-K_COUNT = 9
+           "border": 7, "fields": 8, "population": 9}
+K_COUNT = 10
 
 
 def library_path():
@@ -80,6 +80,7 @@ def load_library(path=None):
     lib.ftq_batch_propagate.argtypes = [vp, i, ctypes.POINTER(vp)]
     lib.ftq_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     lib.ftq_fields.argtypes = [vp, i, i, vp]
+    lib.ftq_population_control.argtypes = [vp, d, vp]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]
@@ -201,6 +202,15 @@ class Propagator:
         self._check(self.lib.ftq_fields(self.h, first_slice, n_slices, ctypes.c_void_p(out.data_ptr())),
                     "ftq_fields")
         return out
+
+    def population_control(self, xi):
+        """Comb the walkers with the uniform draw xi in [0, 1); returns the
+        parent of every slot (CUDA int32 [W])."""
+        t = self._torch
+        parent = t.empty(self.W, dtype=t.int32, device="cuda")
+        self._check(self.lib.ftq_population_control(self.h, float(xi), ctypes.c_void_p(parent.data_ptr())),
+                    "ftq_population_control")
+        return parent
 
     def stabilise(self):
         self._check(self.lib.ftq_stabilise(self.h), "ftq_stabilise")

@@ -42,7 +42,7 @@ void free_all(ftq_ctx* c) {
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
-                    c->tab.hf, c->phi32, c->xbuf, c->xsum};
+                    c->tab.hf, c->phi32, c->xbuf, c->xsum, c->pc_w, c->pc_cnt, c->pc_parent, c->pc_pairs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -119,6 +119,10 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     chk(dalloc(c, &c->htau, W * M));
     chk(dalloc(c, &c->perm, W * M));
     chk(dalloc(c, &c->wstate, W * ftq::WSTRIDE));
+    chk(dalloc(c, &c->pc_w, W));
+    chk(dalloc(c, &c->pc_cnt, W));
+    chk(dalloc(c, &c->pc_parent, W));
+    chk(dalloc(c, &c->pc_pairs, 1 + 2 * W));
     chk(dalloc(c, &c->est, W * ftq::WSTRIDE));
     chk(dalloc(c, &c->red, 16));
     chk(dalloc(c, &c->status, 1));
@@ -172,6 +176,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
 
 int ftq_reset(ftq_ctx* c) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    c->resampled = false;
     cudaError_t e = ftq::launch_init_walkers(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "reset");
     return FTQ_OK;
@@ -222,6 +227,18 @@ int ftq_fields(ftq_ctx* c, int first_slice, int n_slices, double* out_dev) {
     return FTQ_OK;
 }
 
+int ftq_population_control(ftq_ctx* c, double xi, int* parent_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!c->members.empty()) return fail(c, FTQ_EINVAL, "comb the members of a batch one by one");
+    if (!(xi >= 0.0 && xi < 1.0)) return fail(c, FTQ_EINVAL, "xi must lie in [0, 1)");
+    if (c->opts.constraint == FTQ_FREE) return fail(c, FTQ_EINVAL, "the comb acts on phaseless weights");
+    if (c->W > 65535) return fail(c, FTQ_EINVAL, "at most 65535 walkers");
+    cudaError_t e = ftq::launch_population_control(c, xi, parent_dev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "population control");
+    c->resampled = true;
+    return FTQ_OK;
+}
+
 int ftq_stabilise(ftq_ctx* c) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
     cudaError_t e = ftq::launch_qrcp(c);
@@ -252,6 +269,8 @@ int ftq_mu_grad(ftq_ctx* c, double* out_host, double* per_walker_dev) {
     if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
     if (c->k != c->sys.n_slices)
         return fail(c, FTQ_EINVAL, "the mu derivative is accumulated over a whole path: propagate to tau = beta first");
+    if (c->resampled)
+        return fail(c, FTQ_EINVAL, "the mu derivative at fixed draws is undefined across population control");
     cudaError_t e = ftq::launch_mu_grad(c, per_walker_dev);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out_host, c->red + 8, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream);

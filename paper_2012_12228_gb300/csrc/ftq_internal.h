@@ -110,6 +110,12 @@ struct ftq_ctx {
     double2* hh = nullptr;        // Householder u_0 per column                [W][M]
     double* htau = nullptr;       // Householder tau                           [W][M]
     double* xsum = nullptr;       // Re + Im of the T^-1 update's X (mixed)    [W][M][M]
+    // population control: scaled weights, copy counts, parents, copy list [1 + 2W]
+    double* pc_w = nullptr;
+    int* pc_cnt = nullptr;
+    int* pc_parent = nullptr;
+    int* pc_pairs = nullptr;
+    bool resampled = false;       // a comb happened since the last reset
     int* perm = nullptr;          // pivot permutation scratch                 [W][M]
     double* wstate = nullptr;     // [W][WSTRIDE] per-walker state (layout above)
     double* est = nullptr;        // [W][WSTRIDE] per-walker estimators
@@ -165,6 +171,7 @@ struct LaunchScope {
 // Kernel launchers (fp64_kernels.cu).  All asynchronous on ctx->stream.
 cudaError_t launch_init_walkers(ftq_ctx* c);
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x);
+cudaError_t launch_population_control(ftq_ctx* c, double xi, int* parent_out);
 cudaError_t launch_philox_fields(double* out, uint64_t seed, uint32_t sys, int k0, int n, int W, int na,
                                  cudaStream_t st);
 cudaError_t launch_chain(ftq_ctx* c);
