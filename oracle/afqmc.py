@@ -251,6 +251,30 @@ def local_energy(sys: UEG, G):
     return sys.E_M + E1 + E2, Nloc
 
 
+def density_correlation(sys: UEG, G):
+    """<rho(Q) rho(-Q)> for every Q != 0 from P = I - G^T (Wick's theorem;
+    readings B, D, E), the numerator of the static structure factor
+    S(Q) = <rho(Q) rho(-Q)> / N (Results, structure factor).
+
+    Contracting a+_{K1+Q} a_K1 a+_{K2-Q} a_K2 gives Gamma_Q (both pairs
+    closed), -Lambda_Q (crossed, same spin) and, from the anticommutator
+    a_K1 a+_{K2-Q} = delta - a+ a, D_Q = 2 sum_{K: K, K+Q in basis} P_{K+Q,K+Q}.
+    Returns (plus, minus): arrays over the half-space q for Q = +q and -q."""
+    P = one_rdm(G)
+    rp, rm = density_sums(sys, P)
+    nh = len(sys.q_half)
+    out = {1: np.zeros(nh, np.complex128), -1: np.zeros(nh, np.complex128)}
+    for q in range(nh):
+        for sgn, pairs in ((1, sys.pairs_plus[q]), (-1, sys.pairs_minus[q])):
+            gam = (2.0 * rp[q]) * (2.0 * rm[q])
+            b, c = _shifted_pairs(sys, sgn, q)
+            a, d = pairs[:, 0], pairs[:, 1]                  # (a, d) = (K + Q, K)
+            lam = 2.0 * np.sum(P[np.ix_(a, b)] * P[np.ix_(c, d)].T)
+            dq = 2.0 * np.sum(P[a, a])
+            out[sgn][q] = gam - lam + dq
+    return out[1], out[-1]
+
+
 def _shifted_pairs(sys: UEG, sgn, q):
     """Basis indices (b, c) with n_c = n_b - sgn * q_half[q], both in the basis
     (the pair lists read back in the opposite orientation)."""
