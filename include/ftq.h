@@ -101,6 +101,22 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
  * FTQ_EINVAL on a window outside [0, n).  Asynchronous on the context stream. */
 int ftq_fields(ftq_ctx* ctx, int first_slice, int n_slices, double* out_dev);
 
+/* Density correlations for the static structure factor
+ * S(Q) = <rho(Q) rho(-Q)> / N (Results, structure factor) at the current tau,
+ * from P = I - G^T by Wick's theorem: per walker
+ * <rho(Q) rho(-Q)> = Gamma_Q - Lambda_Q + D_Q with Gamma_Q = (2 rho_Q)(2 rho_-Q),
+ * Lambda_Q the exchange sum of the energy estimator and
+ * D_Q = 2 sum_{K: K, K+Q in basis} P_{K+Q,K+Q}; and the weighted sums over walkers.
+ * Q runs over the 2 N_alpha/2 = N_alpha transfers in slot order: index
+ * 2 q is +q and 2 q + 1 is -q for the half-space transfer q of ftq_transfers().
+ *   out_host        host, 4 + 2 N_alpha doubles: {Re sum w, Im sum w, s, n_alive,
+ *                   then Re, Im of sum w <rho(Q) rho(-Q)> for every Q}, every w
+ *                   scaled by exp(-s), s = max ln|w_i| over live walkers
+ *   per_walker_dev  nullable device complex128 [W][N_alpha]: <rho(Q) rho(-Q)>
+ * Allocates its work buffers (W x N_alpha complex128) on the first call.
+ * Synchronises the stream. */
+int ftq_structure_factor(ftq_ctx* ctx, double* out_host, void* per_walker_dev);
+
 /* Comb population control between slices (Computational Details: the comb
  * method).  With the phaseless weights w_i = exp(ln|w_i| - max ln|w|) of the
  * alive walkers (dead walkers weigh 0) and their running sums C_i in index

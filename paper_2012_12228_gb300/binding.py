@@ -38,7 +38,7 @@ class System(ctypes.Structure):
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
-           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control",
+           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control", "ftq_structure_factor",
            "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
            "border": 7, "fields": 8, "population": 9}
@@ -81,6 +81,7 @@ def load_library(path=None):
     lib.ftq_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     lib.ftq_fields.argtypes = [vp, i, i, vp]
     lib.ftq_population_control.argtypes = [vp, d, vp]
+    lib.ftq_structure_factor.argtypes = [vp, dp, vp]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]
@@ -114,6 +115,7 @@ class Propagator:
         if st != 0:
             raise FTQError(f"ftq_init_ueg: {self.lib.ftq_last_error(None).decode()} (status {st})")
         self.h = h
+        self.N = N
         self.W = walkers
         self.M = self.query("M")
         self.n_alpha = self.query("N_ALPHA")
@@ -202,6 +204,32 @@ class Propagator:
         self._check(self.lib.ftq_fields(self.h, first_slice, n_slices, ctypes.c_void_p(out.data_ptr())),
                     "ftq_fields")
         return out
+
+    def structure_factor(self, per_walker=False):
+        """Weighted <rho(Q) rho(-Q)> and S(Q) = Re <rho(Q) rho(-Q)> / N-bar at the
+        current tau for every transfer Q (integer vectors in ``q``, +q and -q of
+        each half-space transfer in turn); ``per_walker`` adds the per-walker
+        values (CUDA complex128 [W][N_alpha])."""
+        import numpy as np
+        t = self._torch
+        nq = self.n_alpha
+        buf = (ctypes.c_double * (4 + 2 * nq))()
+        pw = t.empty((self.W, nq), dtype=t.complex128, device="cuda") if per_walker else None
+        self._check(self.lib.ftq_structure_factor(self.h, buf, None if pw is None else ctypes.c_void_p(pw.data_ptr())),
+                    "ftq_structure_factor")
+        vals = np.frombuffer(buf, dtype=np.float64)
+        sw = complex(vals[0], vals[1])
+        rr = (vals[4::2] + 1j * vals[5::2]) / sw
+        qh = (ctypes.c_int32 * (3 * (nq // 2)))()
+        self._check(self.lib.ftq_transfers(self.h, qh), "ftq_transfers")
+        qh = np.frombuffer(qh, dtype=np.int32).reshape(-1, 3)
+        q = np.empty((nq, 3), dtype=np.int32)
+        q[0::2], q[1::2] = qh, -qh
+        res = {"rhorho": rr, "S": rr.real / self.N, "q": q, "sum_w": sw, "log_scale": vals[2],
+               "n_alive": int(vals[3])}
+        if pw is not None:
+            res["per_walker"] = pw
+        return res
 
     def population_control(self, xi):
         """Comb the walkers with the uniform draw xi in [0, 1); returns the

@@ -42,7 +42,8 @@ void free_all(ftq_ctx* c) {
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
-                    c->tab.hf, c->phi32, c->xbuf, c->xsum, c->pc_w, c->pc_cnt, c->pc_parent, c->pc_pairs};
+                    c->tab.hf, c->phi32, c->xbuf, c->xsum, c->pc_w, c->pc_cnt, c->pc_parent, c->pc_pairs,
+                    c->sq_walker, c->sq_w, c->sq_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -224,6 +225,19 @@ int ftq_fields(ftq_ctx* c, int first_slice, int n_slices, double* out_dev) {
     cudaError_t e = ftq::launch_philox_fields(out_dev, c->opts.seed, 0u, first_slice, n_slices, c->W,
                                               c->sys.n_alpha, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "fields");
+    return FTQ_OK;
+}
+
+int ftq_structure_factor(ftq_ctx* c, double* out_host, void* per_walker_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
+    if (!c->members.empty()) return fail(c, FTQ_EINVAL, "evaluate the members of a batch one by one");
+    cudaError_t e = ftq::launch_structure_factor(c, static_cast<double*>(per_walker_dev));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, c->sq_out, sizeof(double) * (4 + 2 * (size_t)(c->nslot - 1)),
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "structure factor");
     return FTQ_OK;
 }
 

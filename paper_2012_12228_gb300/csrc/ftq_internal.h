@@ -116,6 +116,10 @@ struct ftq_ctx {
     int* pc_parent = nullptr;
     int* pc_pairs = nullptr;
     bool resampled = false;       // a comb happened since the last reset
+    // structure factor: per-walker <rho(Q) rho(-Q)>, weights, reduced sums (allocated on first use)
+    double2* sq_walker = nullptr;
+    double2* sq_w = nullptr;
+    double* sq_out = nullptr;
     int* perm = nullptr;          // pivot permutation scratch                 [W][M]
     double* wstate = nullptr;     // [W][WSTRIDE] per-walker state (layout above)
     double* est = nullptr;        // [W][WSTRIDE] per-walker estimators
@@ -172,6 +176,7 @@ struct LaunchScope {
 cudaError_t launch_init_walkers(ftq_ctx* c);
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x);
 cudaError_t launch_population_control(ftq_ctx* c, double xi, int* parent_out);
+cudaError_t launch_structure_factor(ftq_ctx* c, double* per_walker_out);
 cudaError_t launch_philox_fields(double* out, uint64_t seed, uint32_t sys, int k0, int n, int W, int na,
                                  cudaStream_t st);
 cudaError_t launch_chain(ftq_ctx* c);
