@@ -14,6 +14,16 @@ n_i >= 1 keep their slot, the extra copies fill the slots of walkers with
 n_i = 0 (both taken in ascending order); the weights are rescaled in log form,
 ln|w| = ln(S / W) + max_i ln|w_i|, with S over w_i = exp(ln|w_i| - max).
 Only the phaseless (real, non-negative) weights are combed.
+
+Pair branching (the paper's choice for Theta <= 0.25, citing QWalk), read as:
+with weights normalised to their mean, u_i = w_i / (S / W), the heavy walkers
+(u > 2, by decreasing u, ties to the lower index) are paired in turn with the
+light ones (u < 1/2, by increasing u, ties to the lower index); pair k keeps
+the heavy walker a with probability u_a / (u_a + u_b) (draw xi_k < that
+ratio), else the light walker b; the kept walker is copied into the other
+slot and both carry (w_a + w_b) / 2.  Unpaired walkers keep their weights.
+The total weight is conserved exactly and each state's expected weight is
+unchanged.
 """
 import math
 from dataclasses import replace
@@ -68,6 +78,39 @@ def population_control(states, xi):
     S = np.cumsum(w)[-1]
     lw = math.log(S / W) + ref
     new = [replace(states[parent[i]], logw=complex(lw, 0.0), alive=True) for i in range(W)]
+    return new, parent
+
+
+def pair_branch_pairs(weights, draws, high=2.0, low=0.5):
+    """(source, destination, new weight) of every pair for pair branching."""
+    w = np.asarray(weights, dtype=np.float64)
+    W = len(w)
+    mean = np.cumsum(w)[-1] / W
+    u = w / mean
+    heavy = sorted((i for i in range(W) if u[i] > high), key=lambda i: (-u[i], i))
+    light = sorted((i for i in range(W) if u[i] < low), key=lambda i: (u[i], i))
+    out = []
+    for k, (a, b) in enumerate(zip(heavy, light)):
+        keep_a = draws[k] < u[a] / (u[a] + u[b])
+        src, dst = (a, b) if keep_a else (b, a)
+        out.append((src, dst, 0.5 * (w[a] + w[b])))
+    return out
+
+
+def pair_branch(states, draws):
+    """Pair branching of a list of WalkerState with the uniform draws (one per
+    pair, at least W // 2 of them); returns (new states, parent of every slot)."""
+    W = len(states)
+    w, ref = scaled_weights(states)
+    if not np.isfinite(ref):
+        raise ValueError("no walker alive")
+    parent = list(range(W))
+    new = list(states)
+    for src, dst, nw in pair_branch_pairs(w, draws):
+        lw = complex(math.log(nw) + ref, 0.0)
+        new[src] = replace(states[src], logw=lw, alive=True)
+        new[dst] = replace(states[src], logw=lw, alive=True)
+        parent[dst] = src
     return new, parent
 
 

@@ -98,3 +98,43 @@ def test_population_control_copies_states_and_weights():
     for i, p in enumerate(parent):
         assert n[p] >= 1 and np.array_equal(new[i].G, states[p].G) and new[i].alive
         assert new[i].logw == new[0].logw
+
+
+# ------------------------------------------------------------------ pair branching
+def test_pair_branch_conserves_weight_and_thresholds():
+    from oracle.population import pair_branch_pairs
+    rng = np.random.default_rng(9)
+    for W in (8, 64, 500):
+        w = rng.exponential(size=W) ** 2 * (rng.random(W) > 0.1)
+        draws = rng.random(W // 2)
+        pairs = pair_branch_pairs(w, draws)
+        new = w.copy()
+        for src, dst, nw in pairs:
+            new[src] = new[dst] = nw
+        assert abs(new.sum() - w.sum()) < 1e-12 * w.sum()          # total weight exact
+        u = w / w.mean()
+        for src, dst, _ in pairs:                                    # one heavy, one light
+            assert (u[src] > 2 and u[dst] < 0.5) or (u[src] < 0.5 and u[dst] > 2)
+        unpaired = set(range(W)) - {s for s, _, _ in pairs} - {d for _, d, _ in pairs}
+        heavy_left = [i for i in unpaired if u[i] > 2]
+        light_left = [i for i in unpaired if u[i] < 0.5]
+        assert not (heavy_left and light_left)                       # no pairable walkers remain
+
+
+def test_pair_branch_is_unbiased_over_the_draws():
+    """The expected weight carried by each walker's state is unchanged."""
+    from oracle.population import pair_branch_pairs
+    rng = np.random.default_rng(10)
+    W, grid = 30, 2000
+    w = rng.exponential(size=W) ** 3
+    acc = np.zeros(W)
+    for g in range(grid):
+        draws = np.full(W // 2, (g + 0.5) / grid)
+        carried = w.copy()
+        for src, dst, nw in pair_branch_pairs(w, draws):
+            carried[dst] = 0.0
+            carried[src] = 0.0
+        for src, dst, nw in pair_branch_pairs(w, draws):
+            carried[src] += 2 * nw                                   # two copies of src's state
+        acc += carried
+    assert np.max(np.abs(acc / grid - w)) < 2e-3 * w.max()
