@@ -137,6 +137,22 @@ int ftq_structure_factor(ftq_ctx* ctx, double* out_host, void* per_walker_dev);
  * resampling).  Asynchronous on the context stream. */
 int ftq_population_control(ftq_ctx* ctx, double xi, int* parent_dev);
 
+/* Pair-branching population control between slices (Computational Details:
+ * the method used below Theta = 0.25).  With the weights normalised to their
+ * mean, u_i = w_i / (S / W) (w_i as for the comb, S summed in index order),
+ * the heavy walkers (u > 2, by decreasing u, ties to the lower index) are
+ * paired in turn with the light ones (u < 1/2, by increasing u, ties to the
+ * lower index).  Pair k = (a heavy, b light) keeps a when draws[k] <
+ * u_a / (u_a + u_b), else b; the kept walker carries (w_a + w_b) / 2 and its
+ * whole state is copied into the other slot.  Unpaired walkers are unchanged;
+ * the total weight is conserved.
+ *   draws_host  host float64 [W / 2], uniform draws in [0, 1), one per pair
+ *   parent_dev  nullable device int32 [W]: the walker each slot was copied from
+ * FTQ_EINVAL for draws outside [0, 1), free-projection contexts, batch handles
+ * and W > 8192.  ftq_mu_grad is refused afterwards until ftq_reset.
+ * Synchronises the stream (the draws are read before the call returns). */
+int ftq_pair_branch(ftq_ctx* ctx, const double* draws_host, int* parent_dev);
+
 /* Return every walker to tau = 0 (k = 0, unit weights, all alive). */
 int ftq_reset(ftq_ctx* ctx);
 

@@ -114,9 +114,10 @@ def pair_branch(states, draws):
     return new, parent
 
 
-def run_with_population_control(sys, fields, pc_after, xis, opts: Options = None):
+def run_with_population_control(sys, fields, pc_after, xis, opts: Options = None, method="comb"):
     """All walkers slice by slice; after slice k in `pc_after` the population
-    is combed with the next draw of `xis`.  Returns the final states."""
+    is combed (method "comb": the next draw of `xis`) or pair-branched
+    ("pair": the next array of draws).  Returns the final states."""
     opts = opts or Options()
     n, W = fields.shape[0], fields.shape[1]
     states = [initial_state(sys) for _ in range(W)]
@@ -124,5 +125,6 @@ def run_with_population_control(sys, fields, pc_after, xis, opts: Options = None
     for k in range(1, n + 1):
         states = [slice_step(sys, st, fields[k - 1, w], k, opts)[0] for w, st in enumerate(states)]
         if k in pc_after:
-            states, _ = population_control(states, next(draws))
+            step = population_control if method == "comb" else pair_branch
+            states, _ = step(states, next(draws))
     return states

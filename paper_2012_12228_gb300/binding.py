@@ -38,7 +38,7 @@ class System(ctypes.Structure):
 EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise", "ftq_green",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
-           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control", "ftq_structure_factor",
+           "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control", "ftq_structure_factor", "ftq_pair_branch",
            "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
            "border": 7, "fields": 8, "population": 9}
@@ -82,6 +82,7 @@ def load_library(path=None):
     lib.ftq_fields.argtypes = [vp, i, i, vp]
     lib.ftq_population_control.argtypes = [vp, d, vp]
     lib.ftq_structure_factor.argtypes = [vp, dp, vp]
+    lib.ftq_pair_branch.argtypes = [vp, dp, vp]
     lib.ftq_last_error.argtypes = [vp]
     lib.ftq_last_error.restype = ctypes.c_char_p
     lib.ftq_destroy.argtypes = [vp]
@@ -230,6 +231,19 @@ class Propagator:
         if pw is not None:
             res["per_walker"] = pw
         return res
+
+    def pair_branch(self, draws):
+        """Pair branching with uniform draws in [0, 1) (one per pair, W // 2 of
+        them); returns the parent of every slot (CUDA int32 [W])."""
+        import numpy as np
+        t = self._torch
+        d = np.ascontiguousarray(np.asarray(draws, dtype=np.float64)[: self.W // 2])
+        if d.size < self.W // 2:
+            raise FTQError(f"pair branching needs {self.W // 2} draws")
+        parent = t.empty(self.W, dtype=t.int32, device="cuda")
+        self._check(self.lib.ftq_pair_branch(self.h, d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             ctypes.c_void_p(parent.data_ptr())), "ftq_pair_branch")
+        return parent
 
     def population_control(self, xi):
         """Comb the walkers with the uniform draw xi in [0, 1); returns the

@@ -241,6 +241,20 @@ int ftq_structure_factor(ftq_ctx* c, double* out_host, void* per_walker_dev) {
     return FTQ_OK;
 }
 
+int ftq_pair_branch(ftq_ctx* c, const double* draws_host, int* parent_dev) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!draws_host) return fail(c, FTQ_EINVAL, "draws_host must not be NULL");
+    if (!c->members.empty()) return fail(c, FTQ_EINVAL, "branch the members of a batch one by one");
+    if (c->opts.constraint == FTQ_FREE) return fail(c, FTQ_EINVAL, "pair branching acts on phaseless weights");
+    if (c->W > 8192) return fail(c, FTQ_EINVAL, "pair branching holds at most 8192 walkers");
+    for (int k = 0; k < c->W / 2; ++k)
+        if (!(draws_host[k] >= 0.0 && draws_host[k] < 1.0)) return fail(c, FTQ_EINVAL, "draws must lie in [0, 1)");
+    cudaError_t e = ftq::launch_pair_branch(c, draws_host, parent_dev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pair branching");
+    c->resampled = true;
+    return FTQ_OK;
+}
+
 int ftq_population_control(ftq_ctx* c, double xi, int* parent_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
     if (!c->members.empty()) return fail(c, FTQ_EINVAL, "comb the members of a batch one by one");

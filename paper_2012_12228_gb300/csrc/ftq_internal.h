@@ -176,6 +176,7 @@ struct LaunchScope {
 cudaError_t launch_init_walkers(ftq_ctx* c);
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x);
 cudaError_t launch_population_control(ftq_ctx* c, double xi, int* parent_out);
+cudaError_t launch_pair_branch(ftq_ctx* c, const double* draws_host, int* parent_out);
 cudaError_t launch_structure_factor(ftq_ctx* c, double* per_walker_out);
 cudaError_t launch_philox_fields(double* out, uint64_t seed, uint32_t sys, int k0, int n, int W, int na,
                                  cudaStream_t st);

@@ -94,6 +94,90 @@ __global__ void k_comb(double* __restrict__ ws, double* __restrict__ wsc_g, int*
     for (int p = 0; p < np; ++p) parent[pairs[1 + W + p]] = pairs[1 + p];
 }
 
+// Pair branching (QWalk's method, which the paper uses for Theta <= 0.25),
+// one block: u_i = w_i / (S / W) with S summed in index order by one thread;
+// heavy walkers (u > 2) ranked by decreasing u and light ones (u < 1/2) by
+// increasing u (ties to the lower index) in parallel; pair k = (k-th heavy a,
+// k-th light b) keeps a when draws[k] < u_a / (u_a + u_b), else b; the kept
+// walker gets weight (w_a + w_b) / 2 and is copied into the other slot.
+__global__ void k_pair_branch(double* __restrict__ ws, const double* __restrict__ draws,
+                              int* __restrict__ parent, int* __restrict__ pairs, int W, int* __restrict__ status) {
+    __shared__ double shm[32];
+    __shared__ double mean_sh;
+    __shared__ int nh_sh, nl_sh;
+    extern __shared__ unsigned char smem_raw[];
+    double* wsc = reinterpret_cast<double*>(smem_raw);     // [W] scaled weights
+    double* u = wsc + W;                                   // [W] weights over their mean
+    int* heavy = reinterpret_cast<int*>(u + W);            // [W] heavy walker of rank r
+    int* light = heavy + W;                                // [W] light walker of rank r
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double m = -INFINITY;
+    for (int i = tid; i < W; i += nt) {
+        const double* s = ws + (long)WSTRIDE * i;
+        if (s[2] > 0.5 && s[0] > m) m = s[0];
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) shm[tid >> 5] = m;
+    if (tid == 0) nh_sh = nl_sh = 0;
+    __syncthreads();
+    double ref = shm[0];
+    for (int i = 1; i < (nt + 31) / 32; ++i) ref = fmax(ref, shm[i]);
+    if (!(ref > -INFINITY)) {
+        if (tid == 0) {
+            atomicOr(status, 1);
+            pairs[0] = 0;
+        }
+        for (int i = tid; i < W; i += nt) parent[i] = i;
+        return;
+    }
+    for (int i = tid; i < W; i += nt) {
+        const double* s = ws + (long)WSTRIDE * i;
+        wsc[i] = s[2] > 0.5 ? exp(s[0] - ref) : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double S = 0.0;
+        for (int i = 0; i < W; ++i) S += wsc[i];
+        mean_sh = S / (double)W;
+    }
+    __syncthreads();
+    const double mean = mean_sh;
+    for (int i = tid; i < W; i += nt) {
+        u[i] = wsc[i] / mean;
+        parent[i] = i;
+    }
+    __syncthreads();
+    for (int i = tid; i < W; i += nt) {
+        const double ui = u[i];
+        if (ui > 2.0) {
+            int r = 0;
+            for (int j = 0; j < W; ++j) r += (u[j] > 2.0 && (u[j] > ui || (u[j] == ui && j < i))) ? 1 : 0;
+            heavy[r] = i;
+            atomicAdd(&nh_sh, 1);
+        } else if (ui < 0.5) {
+            int r = 0;
+            for (int j = 0; j < W; ++j) r += (u[j] < 0.5 && (u[j] < ui || (u[j] == ui && j < i))) ? 1 : 0;
+            light[r] = i;
+            atomicAdd(&nl_sh, 1);
+        }
+    }
+    __syncthreads();
+    const int np = min(nh_sh, nl_sh);
+    for (int k = tid; k < np; k += nt) {
+        const int a = heavy[k], b = light[k];
+        const bool keep_a = draws[k] < u[a] / (u[a] + u[b]);
+        const int src = keep_a ? a : b, dst = keep_a ? b : a;
+        double* s = ws + (long)WSTRIDE * src;
+        s[0] = log(0.5 * (wsc[a] + wsc[b])) + ref;
+        s[1] = 0.0;
+        s[2] = 1.0;
+        pairs[1 + k] = src;
+        pairs[1 + W + k] = dst;
+        parent[dst] = src;
+    }
+    if (tid == 0) pairs[0] = np;
+}
+
 __global__ void k_copy_walkers(const int* __restrict__ pairs, CopyPlan plan, int W) {
     const int p = blockIdx.y;
     if (p >= pairs[0]) return;
@@ -115,8 +199,7 @@ __global__ void k_copy_walkers(const int* __restrict__ pairs, CopyPlan plan, int
 
 }  // namespace
 
-cudaError_t launch_population_control(ftq_ctx* c, double xi, int* parent_out) {
-    const int W = c->W;
+static CopyPlan walker_state_plan(ftq_ctx* c) {
     const long MM = (long)c->M * c->M;
     CopyPlan plan{};
     auto add = [&](void* p, long words) {
@@ -136,6 +219,12 @@ cudaError_t launch_population_control(ftq_ctx* c, double xi, int* parent_out) {
     add(c->G, 2 * MM);
     add(c->DR, 2L * c->M);
     add(c->wstate, WSTRIDE);
+    return plan;
+}
+
+cudaError_t launch_population_control(ftq_ctx* c, double xi, int* parent_out) {
+    const int W = c->W;
+    const CopyPlan plan = walker_state_plan(c);
     {
         LaunchScope ls(c, FTQ_K_POPULATION);
         const size_t sm = (sizeof(double) + sizeof(int)) * (size_t)W;
@@ -154,6 +243,35 @@ cudaError_t launch_population_control(ftq_ctx* c, double xi, int* parent_out) {
     e = cudaGetLastError();
     if (e == cudaSuccess && parent_out)
         e = cudaMemcpyAsync(parent_out, c->pc_parent, sizeof(int) * W, cudaMemcpyDeviceToDevice, c->stream);
+    return e;
+}
+
+cudaError_t launch_pair_branch(ftq_ctx* c, const double* draws_host, int* parent_out) {
+    const int W = c->W;
+    const CopyPlan plan = walker_state_plan(c);
+    // the draws go through the comb's weight scratch (W doubles >= W / 2 draws)
+    cudaError_t e = cudaMemcpyAsync(c->pc_w, draws_host, sizeof(double) * (size_t)(W / 2), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return e;
+    const size_t sm = (2 * sizeof(double) + 2 * sizeof(int)) * (size_t)W;
+    if (sm > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_pair_branch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        LaunchScope ls(c, FTQ_K_POPULATION);
+        k_pair_branch<<<1, 256, sm, c->stream>>>(c->wstate, c->pc_w, c->pc_parent, c->pc_pairs, W, c->status);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls(c, FTQ_K_POPULATION);
+        k_copy_walkers<<<dim3(32, (unsigned)W), 256, 0, c->stream>>>(c->pc_pairs, plan, W);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess && parent_out)
+        e = cudaMemcpyAsync(parent_out, c->pc_parent, sizeof(int) * W, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);    // the host draws are read before return
     return e;
 }
 

@@ -124,3 +124,66 @@ def test_rejected_arguments(ftq):
     with pytest.raises(ftq.FTQError):
         q.population_control(0.5)
     q.close()
+
+
+# ------------------------------------------------------------------ pair branching
+def oracle_pair_parents(lw, alive, draws):
+    from oracle.population import pair_branch_pairs
+    ref = np.max(np.where(alive, lw, -np.inf))
+    w = np.where(alive, np.exp(lw - ref), 0.0)
+    W = len(w)
+    parent = np.arange(W)
+    new_lw = np.where(alive, lw, np.nan)
+    pairs = pair_branch_pairs(w, draws)
+    for src, dst, nw in pairs:
+        parent[dst] = src
+        new_lw[src] = new_lw[dst] = math.log(nw) + ref
+    u = w / (np.cumsum(w)[-1] / W)
+    margin = min(np.min(np.abs(u - 2.0)), np.min(np.abs(u[u > 0] - 0.5)))
+    for k, (src, dst, _) in enumerate(pairs):
+        a, b = (src, dst) if u[src] > 2 else (dst, src)
+        margin = min(margin, abs(draws[k] - u[a] / (u[a] + u[b])))
+    return parent, new_lw, margin, len(pairs)
+
+
+def test_pair_branch_matches_oracle(ftq):
+    p = make(ftq, "ueg_n14_m57", 64)
+    p.propagate(torch.from_numpy(gaussian_fields(23, 30, 64, p.n_alpha)).cuda())
+    ws = p.weights().cpu().numpy()
+    lw, alive = ws[:, 0], ws[:, 2] > 0.5
+    draws = np.random.default_rng(2).random(32)
+    ref_parent, ref_lw, margin, npairs = oracle_pair_parents(lw, alive, draws)
+    assert margin > 1e-9 and npairs > 0
+    parent = p.pair_branch(draws).cpu().numpy()
+    assert np.array_equal(parent, ref_parent)
+    ws2 = p.weights().cpu().numpy()
+    touched = np.isfinite(ref_lw)
+    assert np.max(np.abs(ws2[touched, 0] - ref_lw[touched])) < 1e-12 * max(1.0, np.max(np.abs(ref_lw[touched])))
+    assert p.status() == 0
+    p.close()
+
+
+def test_path_with_pair_branching_matches_oracle_fp64(ftq):
+    c = WORKLOADS["ueg_n14_m57"]
+    s = UEG(c["N"], c["M"], c["rs"], c["theta"], c["dtau"])
+    W, n = 24, 30
+    f = gaussian_fields(c["seed"], n, W, s.N_alpha)
+    rng = np.random.default_rng(6)
+    d1, d2 = rng.random(W // 2), rng.random(W // 2)
+    ref = run_with_population_control(s, f, pc_after={10, 20}, xis=(d1, d2), method="pair")
+    p = make(ftq, "ueg_n14_m57", W)
+    fd = torch.from_numpy(f).cuda()
+    p.propagate(fd[:10].contiguous())
+    par1 = p.pair_branch(d1).cpu().numpy()
+    p.propagate(fd[10:20].contiguous())
+    par2 = p.pair_branch(d2).cpu().numpy()
+    p.propagate(fd[20:].contiguous())
+    assert np.any(par1 != np.arange(W)) or np.any(par2 != np.arange(W))
+    G = p.green().cpu().numpy()
+    ws = p.weights().cpu().numpy()
+    for w in range(W):
+        assert np.abs(G[w] - ref[w].G).max() < 1e-10 * np.abs(ref[w].G).max()
+        assert bool(ws[w, 2] > 0.5) == ref[w].alive
+        if ref[w].alive:
+            assert abs(ws[w, 0] - ref[w].logw.real) < 1e-9 * max(1.0, abs(ref[w].logw.real))
+    p.close()
