@@ -43,7 +43,7 @@ void free_all(ftq_ctx* c) {
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
                     c->tab.hf, c->phi32, c->xbuf, c->xsum, c->pc_w, c->pc_cnt, c->pc_parent, c->pc_pairs,
-                    c->sq_walker, c->sq_w, c->sq_out};
+                    c->sq_walker, c->sq_w, c->sq_out, c->Yf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -96,6 +96,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         c->LD = (M + 7) / 8 * 8;
         const size_t wsz = 2 * (size_t)c->LD * 2 * c->Kp;
         chk(dalloc(c, &c->Ypl, W * wsz));
+        chk(dalloc(c, &c->Yf, W * wsz / 2));
         chk(dalloc(c, &c->zpl[0], W * wsz));
         chk(dalloc(c, &c->zpl[1], W * wsz));
         chk(dalloc(c, &c->G32, W * MM));

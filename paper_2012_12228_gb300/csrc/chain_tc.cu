@@ -143,6 +143,8 @@ __device__ __forceinline__ uint32_t idesc_tf32(int n) {
 struct TcArgs {
     const float* Yu;
     float* out;
+    const float* Uf;              // the U term as one FP32 plane per walker
+    float* Of;                    // nullable: the output also as one FP32 plane (last Horner step)
     const float2* phi;            // FP32 field table [W][nslot]
     const uint16_t* vidx;
     const float2* zs;             // scales as (hi, lo) float pairs, nullable
@@ -392,50 +394,54 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
             const size_t rowlen = 2 * (size_t)p.Kp;
             const size_t partoff = (size_t)p.LDc * rowlen;
             const size_t wstride = 2 * partoff;
-            const float* __restrict__ U = p.Yu + wstride * w;
+            const float* __restrict__ U = p.Uf + partoff * w;      // one plane per walker
             float* __restrict__ O = p.out + wstride * w;
+            float* __restrict__ Of = p.Of ? p.Of + partoff * w : nullptr;
             const int cend = min(col0 + p.NT, p.M);
             const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tb_i * tb.ncols);
             const int nch = (p.NT + 15) / 16;
             // U of chunk ch + 1 is loaded while chunk ch is finished, so that two
-            // chunks of loads are in flight per thread
-            float uh[2][16], ul[2][16];
-            auto load_u = [&](int ch, float (&h)[16], float (&l)[16]) {
+            // chunks of loads are in flight per thread; U is read as one FP32
+            // plane (it equals hi + lo of the chain planes exactly)
+            float uf[3][16];
+            auto load_u = [&](int ch, float (&u)[16]) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int c = col0 + ch * 16 + q;
                     const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
-                    const bool ok = row_ok && c < cend;
-                    h[q] = ok ? U[o] : 0.f;
-                    l[q] = ok ? U[partoff + o] : 0.f;
+                    u[q] = (row_ok && c < cend) ? U[o] : 0.f;
                 }
             };
-            auto finish = [&](int ch, const uint32_t (&v)[16], const float (&h)[16], const float (&l)[16]) {
+            auto finish = [&](int ch, const uint32_t (&v)[16], const float (&u)[16]) {
                 if (!row_ok) return;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int c = col0 + ch * 16 + q;
                     if (c < cend) {
                         const size_t o = (size_t)c * rowlen + (size_t)part * p.Kp + i;
-                        const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(h[q] + l[q])));
+                        const float val = osi(fmaf(p.alpha, __uint_as_float(v[q]), usi(u[q])));
                         float hh, ll;
                         split_tf32(val, hh, ll);
                         O[o] = hh;
                         O[partoff + o] = ll;
+                        if (Of) Of[o] = val;
                     }
                 }
             };
             if (acc_ok) {
-                load_u(0, uh[0], ul[0]);
-                for (int ch = 0; ch < nch; ch += 2) {
-                    uint32_t v[16];
-                    tmem_ld16(acc + (uint32_t)(ch * 16), v);
-                    if (ch + 1 < nch) load_u(ch + 1, uh[1], ul[1]);
-                    finish(ch, v, uh[0], ul[0]);
-                    if (ch + 1 < nch) {
-                        tmem_ld16(acc + (uint32_t)((ch + 1) * 16), v);
-                        if (ch + 2 < nch) load_u(ch + 2, uh[0], ul[0]);
-                        finish(ch + 1, v, uh[1], ul[1]);
+#pragma unroll
+                for (int d = 0; d < 3 - 1; ++d)
+                    if (d < nch) load_u(d, uf[d]);
+                for (int ch0 = 0; ch0 < nch; ch0 += 3) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const int ch = ch0 + d;
+                        if (ch < nch) {
+                            if (ch + 3 - 1 < nch) load_u(ch + 3 - 1, uf[(d + 3 - 1) % 3]);
+                            uint32_t v[16];
+                            tmem_ld16(acc + (uint32_t)(ch * 16), v);
+                            finish(ch, v, uf[d]);
+                        }
                     }
                 }
             }
@@ -613,6 +619,8 @@ bool fill_args(ftq_ctx* c, const float* zin, float* out, const double* zs, const
     tc_plan(c->M, c->nct, &R, &NT);
     a->Yu = c->Ypl;
     a->out = out;
+    a->Uf = c->Yf;
+    a->Of = os ? c->Yf : nullptr;         // the last Horner step's output becomes the new Y
     a->phi = c->phi32;
     a->vidx = c->tab.vidx;
     a->zs = zs ? c->tab.hf : nullptr;     // the only scale the chain uses is h

@@ -87,6 +87,7 @@ struct ftq_ctx {
     // per walker [hi re | hi im | lo re | lo im], each Kp x LD, zero padded
     int Kp = 0, LD = 0;
     float* Ypl = nullptr;
+    float* Yf = nullptr;          // the chain as one FP32 plane (= hi + lo) at the tensor-core tile entries
     float* zpl[2] = {nullptr, nullptr};
     float2* G32 = nullptr;        // G(tau_k) for k < n, complex64            [W][M][M]
     float2* w32 = nullptr;        // FP32 LU workspace                        [W][M][M]

@@ -344,12 +344,14 @@ cudaError_t mixed_init(ftq_ctx* c) {
     const int M = c->M, W = c->W;
     const size_t ws = walker_stride(c);
     cudaError_t e = cudaMemsetAsync(c->Ypl, 0, sizeof(float) * ws * W, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->Yf, 0, sizeof(float) * (ws / 2) * W, c->stream);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(c->zpl[b], 0, sizeof(float) * ws * W, c->stream);
     if (e != cudaSuccess) return e;
     {
         LaunchScope ls(c, FTQ_K_INIT);
         long n = (long)W * M;
         k_planes_identity<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->Ypl, c->Kp, M, ws, W);
+        k_planes_identity<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->Yf, c->Kp, M, ws / 2, W);
     }
     {
         LaunchScope ls(c, FTQ_K_INIT);

@@ -214,6 +214,7 @@ static CopyPlan walker_state_plan(ftq_ctx* c) {
     } else {
         add(c->Ypl, (long)c->LD * 2 * c->Kp);                 // two planes of LD x 2 Kp floats
         add(c->G32, MM);                                       // float2 = one word
+        add(c->Yf, (long)c->LD * c->Kp);                       // one plane of LD x 2 Kp floats
     }
     add(c->Tinv, 2 * MM);
     add(c->G, 2 * MM);

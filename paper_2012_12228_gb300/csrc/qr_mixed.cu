@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
 // Q[:, c0 .. c0+32) = H_0 ... H_{M-1} e_c, accumulated backwards in shared
 // memory (reflector j only touches rows >= j and columns >= j).
 __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT, const double* __restrict__ htau,
-                                                 float* __restrict__ Ypl, int M, Planes P, size_t wstride) {
+                                                 float* __restrict__ Ypl, float* __restrict__ Yf, int M, Planes P,
+                                                 size_t wstride) {
     extern __shared__ unsigned char smem_raw[];
     float2* Qp = reinterpret_cast<float2*>(smem_raw);     // [M][QP]
     float2* ub = Qp + (size_t)M * QP;                     // [M]
@@ -313,7 +314,11 @@ __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT,
     float* Yw = Ypl + wstride * w;
     for (int e = tid; e < ncol * M; e += blockDim.x) {
         const int c = e / M, i = e % M;
-        P.store(Yw, i, c0 + c, Qp[i * QP + c]);
+        const float2 q = Qp[i * QP + c];
+        P.store(Yw, i, c0 + c, q);
+        float* f = Yf + P.part * w + (size_t)(c0 + c) * (2 * P.Kp) + i;     // same value, one plane
+        f[0] = q.x;
+        f[P.Kp] = q.y;
     }
 }
 
@@ -344,7 +349,7 @@ cudaError_t launch_qr_prepiv(ftq_ctx* c) {
     }
     LaunchScope ls(c, FTQ_K_BRIDGE);
     k_form_q32<<<dim3((unsigned)((M + QP - 1) / QP), (unsigned)c->W), 256, sm2, c->stream>>>(c->w2_32, c->htau,
-                                                                                          c->Ypl, M, P, ws);
+                                                                                          c->Ypl, c->Yf, M, P, ws);
     return cudaGetLastError();
 }
 
