@@ -46,6 +46,18 @@ P  P(tau) in the optimal force bias is the equal-time one-body density
    as with no force bias).  At tau = beta both forms coincide, so the
    estimators are unchanged.
 
+S  Modified overlap ratio (Eq. ztfix; proposed in the T -> 0 discussion, not
+   evaluated there).  With Options(overlap="modified") the trial block is
+   B_T^n at every slice, A~_k = B_T^n B_k ... B_1, and the weight uses
+   S~_k = [det(I + A~_k) / det(I + A~_{k-1})]^2 in place of S_k (theta_k =
+   arg S~_k); the force bias is the optimal one for S~ (reading P with
+   D_L = B_T^n).  The target stays the physical ensemble: after slice n the
+   estimators use G(beta) = (I + R_n)^-1 and the weight takes one more ratio
+   r = [det(I + R_n) / det(I + B_T^n R_n)]^2, projected like a slice ratio
+   (|r| max(0, cos arg r) phaseless, r in free projection), with no Gaussian
+   factor.  In free projection with no force bias the final weight equals
+   the Eq. ftoratio one exactly (both telescope to the same determinants).
+
 Slice bookkeeping (Eq. Abrenda): before slice k the right block
 R_{k-1} = B_{k-1} ... B_1 is held as Y D T (Y = B's since the last QRCP times
 Q_R); the left block is the diagonal D_L = B_T^(n-(k-1)).  Slice k: force
@@ -289,6 +301,7 @@ class Options:
     stabilise_every: int = 5
     exp_order: int = 6
     constraint: str = "phaseless"      # or "free"
+    overlap: str = "paper"             # "paper" (Eq. ftoratio) | "modified" (Eq. ztfix)
     green: str = "paper"               # "paper" | "two_sided" | "direct"
     exact_exp: bool = False
     force_bias: bool = True
@@ -328,10 +341,25 @@ def initial_state(sys: UEG):
                        np.eye(M, dtype=np.complex128), G, complex(np.sum(np.log1p(dl))))
 
 
+def update_weight(logw, alive, lnS, gauss, constraint):
+    """w <- |I| max(0, cos theta) with I = S e^gauss, theta = arg S (Eqs.
+    import, phimport, theta; reading K), or w <- w I in free projection."""
+    if constraint == "free":
+        return logw + lnS + gauss, alive
+    if alive:
+        c = math.cos(lnS.imag)                      # theta_k = arg S_k
+        if c <= 0.0:
+            return logw, False
+        return logw + lnS.real + gauss.real + math.log(c), alive
+    return logw, alive
+
+
 def slice_step(sys: UEG, st: WalkerState, x, k, opts: Options, xbar=None):
     """Slice k (1-based) of Eq. Abrenda: force bias from G_{k-1}, B_k from the
     shifted field, Y <- B_k Y, QRCP every s slices, G_k and ln det, then the
-    phaseless (Eqs. import, phimport, theta) or free-projection weight.
+    phaseless (Eqs. import, phimport, theta) or free-projection weight.  With
+    the modified overlap (Eq. ztfix, reading S) the trial block stays B_T^n
+    and slice n ends with the physical G(beta) and the ratio r.
 
     Returns (new state, lnS_k, gauss_k, xbar_k)."""
     x = np.asarray(x, dtype=np.float64)
@@ -341,18 +369,15 @@ def slice_step(sys: UEG, st: WalkerState, x, k, opts: Options, xbar=None):
     Y, D, T = B @ st.Y, st.D, st.T
     if opts.stabilise_every > 0 and k % opts.stabilise_every == 0:
         Y, D, T = stabilise(Y, D, T)
-    Gn, ldn = GREEN[opts.green](left_diagonal(sys, k), Y, D, T)
+    modified = opts.overlap == "modified"
+    Gn, ldn = GREEN[opts.green](left_diagonal(sys, 0 if modified else k), Y, D, T)
     lnS = 2.0 * (ldn - st.logdet)                  # two identical spin blocks
     gauss = np.sum(x * xbar - 0.5 * xbar * xbar)   # Eq. import
-    logw, alive = st.logw, st.alive
-    if opts.constraint == "free":
-        logw = logw + lnS + gauss
-    elif alive:
-        c = math.cos(lnS.imag)                      # theta_k = arg S_k
-        if c <= 0.0:
-            alive = False
-        else:
-            logw = logw + lnS.real + gauss.real + math.log(c)
+    logw, alive = update_weight(st.logw, st.alive, lnS, gauss, opts.constraint)
+    if modified and k == sys.n_slices:
+        Gp, ldp = GREEN[opts.green](left_diagonal(sys, k), Y, D, T)
+        logw, alive = update_weight(logw, alive, 2.0 * (ldp - ldn), 0j, opts.constraint)
+        Gn, ldn = Gp, ldp
     return WalkerState(Y, D, T, Gn, ldn, logw, alive), lnS, gauss, xbar
 
 
