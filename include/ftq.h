@@ -52,6 +52,17 @@ extern "C" {
 #define FTQ_PHASELESS 0   /* w <- |I_k| max(0, cos theta_k)  (Eqs. import, phimport, theta) */
 #define FTQ_FREE      1   /* w <- w I_k, complex (unconstrained free projection)            */
 
+/* overlap ratio the weight update and the force bias are built on */
+#define FTQ_OVERLAP_PAPER    0  /* S_k of Eq. ftoratio: A_k = B_T^(n-k) B_k ... B_1            */
+#define FTQ_OVERLAP_MODIFIED 1  /* S~_k of Eq. ztfix: A~_k = B_T^n B_k ... B_1 at every slice;
+                                   after slice n the library evaluates G(beta) and
+                                   ln det(I + B_n ... B_1) of the physical ensemble and
+                                   multiplies each weight by the ratio
+                                   r = [det(I + B_n...B_1) / det(I + B_T^n B_n...B_1)]^2,
+                                   projected as a slice ratio (|r| max(0, cos arg r) under
+                                   FTQ_PHASELESS, r under FTQ_FREE), so the estimators at
+                                   tau = beta target the physical ensemble               */
+
 typedef struct ftq_ctx ftq_ctx;
 
 typedef struct {
@@ -60,7 +71,7 @@ typedef struct {
     int      exp_order;        /* p >= 1: Taylor order of exp(V)                          */
     int      precision;        /* FTQ_FP64, FTQ_MIXED or FTQ_MIXED_SIMT                   */
     int      constraint;       /* FTQ_PHASELESS or FTQ_FREE                               */
-    int      reserved;         /* must be 0                                               */
+    int      overlap;          /* FTQ_OVERLAP_PAPER or FTQ_OVERLAP_MODIFIED               */
     uint64_t seed;             /* key of the on-device field generator (ftq_fields)       */
     void*    cuda_stream;      /* cudaStream_t the library launches on (NULL = default)  */
     double   force_bias_cap;   /* 0 = off (no cap is applied in this version)             */

@@ -10,6 +10,7 @@ import os
 
 FTQ_FP64, FTQ_MIXED, FTQ_MIXED_SIMT = 0, 1, 2
 FTQ_PHASELESS, FTQ_FREE = 0, 1
+FTQ_OVERLAP_PAPER, FTQ_OVERLAP_MODIFIED = 0, 1
 _Q = dict(M=0, N_ALPHA=1, N_SLICES=2, SLICE=3, WALKERS=4, NCUT2=5, PRECISION=6, DEVICE_BYTES=7)
 _F = dict(BETA=0, DTAU=1, MU=2, MU_T=3, L=4, E_M=5)
 
@@ -24,7 +25,7 @@ class FTQError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("walkers", ctypes.c_int), ("stabilise_every", ctypes.c_int),
                 ("exp_order", ctypes.c_int), ("precision", ctypes.c_int),
-                ("constraint", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("constraint", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
                 ("force_bias_cap", ctypes.c_double)]
 
@@ -101,14 +102,15 @@ class Propagator:
     Parameters mirror ftq_init_ueg; ``mu=None`` selects mu = mu_T."""
 
     def __init__(self, N, M, rs, theta, dtau, mu=None, walkers=64, stabilise_every=5,
-                 exp_order=6, precision=FTQ_FP64, constraint=FTQ_PHASELESS, seed=0, stream=None):
+                 exp_order=6, precision=FTQ_FP64, constraint=FTQ_PHASELESS, seed=0, stream=None,
+                 overlap=FTQ_OVERLAP_PAPER):
         import torch
         if not torch.cuda.is_available():
             raise FTQError("no CUDA device: the propagator has no CPU path")
         self._torch = torch
         self.lib = load_library()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        o = Opts(walkers, stabilise_every, exp_order, precision, constraint, 0, seed,
+        o = Opts(walkers, stabilise_every, exp_order, precision, constraint, overlap, seed,
                  ctypes.c_void_p(self.stream.cuda_stream), 0.0)
         h = ctypes.c_void_p()
         st = self.lib.ftq_init_ueg(ctypes.byref(h), N, M, rs, theta,

@@ -68,7 +68,8 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         return fail(nullptr, FTQ_EINVAL, "unknown precision");
     if (opts->constraint != FTQ_PHASELESS && opts->constraint != FTQ_FREE)
         return fail(nullptr, FTQ_EINVAL, "unknown constraint");
-    if (opts->reserved != 0) return fail(nullptr, FTQ_EINVAL, "reserved field must be 0");
+    if (opts->overlap != FTQ_OVERLAP_PAPER && opts->overlap != FTQ_OVERLAP_MODIFIED)
+        return fail(nullptr, FTQ_EINVAL, "unknown overlap");
     if (N % 2 != 0) return fail(nullptr, FTQ_EINVAL, "N must be even (unpolarised gas)");
     ftq_ctx* c = new (std::nothrow) ftq_ctx();
     if (!c) return fail(nullptr, FTQ_ENOMEM, "host allocation failed");

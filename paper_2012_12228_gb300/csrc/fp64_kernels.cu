@@ -339,7 +339,7 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
                         double2* __restrict__ work2, double2* __restrict__ G,
                         const double* __restrict__ eps, double* __restrict__ ws,
                         int* __restrict__ status, int M, double lscale, double mu_T,
-                        int constraint, int update, double kdt) {
+                        int constraint, int update, int with_gauss, double kdt) {
     extern __shared__ unsigned char smem_raw[];
     double2* drs = reinterpret_cast<double2*>(smem_raw);     // [M]
     double2* invU = drs + M;                                 // [M]
@@ -456,7 +456,7 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
         if (update) {
             double2 lnS = make_double2(2.0 * (ld.x - s[3]), 2.0 * (ld.y - s[4]));
             const double2 dlnS = make_double2(2.0 * (tk.x - s[9]), 2.0 * (tk.y - s[10]));
-            double gr = s[5], gi = s[6];
+            const double gr = with_gauss ? s[5] : 0.0, gi = with_gauss ? s[6] : 0.0;
             if (constraint == FTQ_FREE) {
                 s[0] += lnS.x + gr;
                 s[1] = remainder(s[1] + lnS.y + gi, 2.0 * kPi);
@@ -652,22 +652,31 @@ cudaError_t launch_qrcp(ftq_ctx* c) {
     return e;
 }
 
-cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update) {
+double left_scale(const ftq_ctx* c, int k) {
+    const int power = c->opts.overlap == FTQ_OVERLAP_MODIFIED ? c->sys.n_slices : c->sys.n_slices - k;
+    return (double)power * c->sys.dtau;
+}
+
+cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update, bool physical) {
     const int M = c->M;
     size_t sm = (2 * sizeof(double2) + 3 * sizeof(double) + sizeof(int)) * M;
     int nt = fact_threads(M);
-    double lscale = (double)(c->sys.n_slices - k) * c->sys.dtau;
+    const double lscale = physical ? 0.0 : left_scale(c, k);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     LaunchScope ls(c, FTQ_K_GREEN);
     k_green<<<c->W, nt, sm, c->stream>>>(Y, c->Tinv, c->DR, c->work, c->work2, c->G, c->tab.eps, c->wstate,
                                         c->status, M, lscale, c->sys.mu_T, c->opts.constraint, update ? 1 : 0,
-                                        (double)k * c->sys.dtau);
+                                        physical ? 0 : 1, (double)k * c->sys.dtau);
     return cudaGetLastError();
 }
 
 cudaError_t launch_green(ftq_ctx* c, int k, bool update) {
     if (c->opts.precision != FTQ_FP64) return mixed_green(c, k);
-    return launch_green64(c, c->Y, k, update);
+    cudaError_t e = launch_green64(c, c->Y, k, update);
+    // the modified overlap ends with the physical G(beta) and the ratio r
+    if (e == cudaSuccess && k == c->sys.n_slices && c->opts.overlap == FTQ_OVERLAP_MODIFIED)
+        e = launch_green64(c, c->Y, k, update, true);
+    return e;
 }
 
 cudaError_t launch_estimators(ftq_ctx* c, double* per_walker) {

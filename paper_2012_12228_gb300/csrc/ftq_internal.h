@@ -188,7 +188,13 @@ cudaError_t launch_estimators(ftq_ctx* c, double* per_walker);
 cudaError_t launch_copy_green(ftq_ctx* c, double2* out);
 // complex128 factorisations on explicit buffers
 cudaError_t launch_qrcp64(ftq_ctx* c, const double2* Yin, double2* Qout);
-cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update_weights);
+// physical = true evaluates the physical A(beta) = B_n ... B_1 (no trial block)
+// and takes the overlap ratio without a Gaussian factor (the last step of the
+// modified overlap, Eq. ztfix).
+cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update_weights, bool physical = false);
+// dtau times the power of B_T in the trial block at slice k: n - k for the
+// overlap of Eq. ftoratio, n for the modified overlap of Eq. ztfix.
+double left_scale(const ftq_ctx* c, int k);
 cudaError_t launch_force_bias_any(ftq_ctx* c, const double* x, const void* G, bool g32);
 
 // Mixed-precision launchers (mixed_kernels.cu).

@@ -468,7 +468,7 @@ cudaError_t launch_green32b(ftq_ctx* c, int k) {
     Planes P;
     P.Kp = c->Kp;
     P.part = (size_t)c->LD * 2 * c->Kp;
-    const double lscale = (double)(c->sys.n_slices - k) * c->sys.dtau;
+    const double lscale = left_scale(c, k);
     int nt = (M + 31) / 32 * 32;
     nt = nt < 256 ? 256 : (nt > GT_MAX ? GT_MAX : nt);
     LaunchScope ls(c, FTQ_K_GREEN);

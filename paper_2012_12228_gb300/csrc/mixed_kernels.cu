@@ -405,6 +405,8 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
                 c->Ypl, c->zbuf[1], planes_of(c), M, walker_stride(c), n);
         }
         cudaError_t e = launch_green64(c, c->zbuf[1], k, true);
+        if (e == cudaSuccess && c->opts.overlap == FTQ_OVERLAP_MODIFIED)
+            e = launch_green64(c, c->zbuf[1], k, true, true);
         c->g64_valid = true;
         return e;
     }
@@ -415,7 +417,7 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
     }
     size_t sm = (2 * sizeof(float2) + 3 * sizeof(float) + sizeof(int)) * M;
     int nt = fact_threads(M);
-    double lscale = (double)(c->sys.n_slices - k) * c->sys.dtau;
+    double lscale = left_scale(c, k);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_green32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     LaunchScope ls(c, FTQ_K_GREEN);
     k_green32<<<c->W, nt, sm, c->stream>>>(c->Ypl, c->Tinv, c->DR, c->w32, c->w2_32, c->G32, c->tab.eps, c->wstate,

@@ -47,6 +47,10 @@ def test_argument_errors_without_gpu(lib):
     o.exp_order = 0
     assert lib.ftq_init_ueg(ctypes.byref(h), 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
     o.exp_order = 6
+    o.overlap = 2
+    assert lib.ftq_init_ueg(ctypes.byref(h), 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
+    assert b"overlap" in lib.ftq_last_error(None)
+    o.overlap = 0
     o.walkers = 0
     assert lib.ftq_init_ueg(ctypes.byref(h), 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
     assert lib.ftq_init_ueg(None, 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
