@@ -58,6 +58,22 @@ S  Modified overlap ratio (Eq. ztfix; proposed in the T -> 0 discussion, not
    factor.  In free projection with no force bias the final weight equals
    the Eq. ftoratio one exactly (both telescope to the same determinants).
 
+T  Low-rank truncation (Sec. "Exploiting the low-rank structure", Eq. thresh;
+   threshold absolute, the paper's production value 1e-6).  With
+   Options(low_rank=thr) every stabilisation keeps the leading columns of the
+   pivoted QR whose |R_jj| >= thr (Businger-Golub pivoting makes |R_jj|
+   non-increasing, so Eq. thresh keeps a prefix; at least one), so the right
+   block is R = Y d_R t_R with Y M x m, t_R m x M.  The left block D_L keeps
+   the entries >= thr (m_L of them).  G(tau) = (I + R D_L)^-1 follows the
+   paper's steps in the cyclic order of reading P: core c = d_R t_R[:, L] d_L
+   (m x m_L), its QRCP c = q_c r_c pi_c, q = Y q_c, d = diag r_c,
+   t = (d^-1 r_c)(pi_c P_L^T); then Woodbury and the determinant lemma in
+   m_T = min(m, m_L) dimensions with the scales of d split as in the stable
+   G: I + d t q = d_b^-1 (d_b + d_s X), X = t q, so
+   G = I - q (d_b + d_s X)^-1 d_s t and ln det(I + A) = ln det(d_b + d_s X)
+   - sum ln d_b (the paper splits the same product on the other side of X,
+   (X^-1 d_b + d_s) d_b^-1 X; the two are equal and ours needs no X^-1).
+
 Slice bookkeeping (Eq. Abrenda): before slice k the right block
 R_{k-1} = B_{k-1} ... B_1 is held as Y D T (Y = B's since the last QRCP times
 Q_R); the left block is the diagonal D_L = B_T^(n-(k-1)).  Slice k: force
@@ -239,6 +255,49 @@ def green_direct(DL, Y, D, T):
 GREEN = {"paper": green_paper, "two_sided": green_two_sided, "direct": green_direct}
 
 
+# ---------------------------------------------------------------- low rank (reading T)
+def stabilise_truncated(Y, D, T, thr):
+    """Stratification step of the right block followed by Eq. thresh: QRCP of
+    Y D (M x m), keep the leading columns with |R_jj| >= thr (at least one).
+    Returns Y (M x m'), D (m'), T (m' x M)."""
+    Q, R, piv = sla.qr(Y * D[None, :], pivoting=True, mode="economic")
+    Dn = np.diag(R).copy()
+    Tn = (R / Dn[:, None]) @ T[piv, :]
+    small = np.abs(Dn) < thr
+    m = int(np.argmax(small)) if small.any() else len(Dn)
+    m = max(m, 1)
+    return Q[:, :m], Dn[:m], Tn[:m, :]
+
+
+def left_keep(DL, thr):
+    """Indices of the left block entries kept by Eq. thresh (at least the largest)."""
+    keep = np.nonzero(DL >= thr)[0]
+    return keep if len(keep) else np.array([int(np.argmax(DL))])
+
+
+def green_lowrank(DL, Y, D, T, thr):
+    """G(tau) = (I + R D_L)^-1 and ln det(I + R D_L) with R = Y diag(D) T of rank
+    m and D_L truncated by Eq. thresh (Sec. "Exploiting the low-rank
+    structure"): core c = D T[:, L] d_L, QRCP c = q_c r_c pi_c, q = Y q_c,
+    d = diag r_c, t = (d^-1 r_c)(pi_c P_L^T), X = t q, then the Woodbury
+    identity and the matrix determinant lemma in m_T dimensions."""
+    M = Y.shape[0]
+    L = left_keep(DL, thr)
+    c = D[:, None] * T[:, L] * DL[L][None, :]
+    Qc, R, piv = sla.qr(c, pivoting=True, mode="economic")
+    d = np.diag(R).copy()
+    U = R / d[:, None]
+    q = Y @ Qc
+    t = np.zeros((len(d), M), dtype=np.complex128)
+    t[:, L[piv]] = U
+    X = t @ q
+    Db, Ds = _split(d)
+    Mx = np.diag(Db).astype(np.complex128) + Ds[:, None] * X
+    G = np.eye(M) - q @ np.linalg.solve(Mx, Ds[:, None] * t)
+    ld = _clog_det(Mx) - np.sum(np.log(Db))
+    return G, ld
+
+
 # ---------------------------------------------------------------- estimators
 def local_energy(sys: UEG, G):
     """Local energy eps = E_M + E_1 + E_2 and particle number N from
@@ -302,6 +361,7 @@ class Options:
     exp_order: int = 6
     constraint: str = "phaseless"      # or "free"
     overlap: str = "paper"             # "paper" (Eq. ftoratio) | "modified" (Eq. ztfix)
+    low_rank: float = 0.0              # threshold of Eq. thresh (reading T); 0 = full rank
     green: str = "paper"               # "paper" | "two_sided" | "direct"
     exact_exp: bool = False
     force_bias: bool = True
@@ -330,6 +390,7 @@ class WalkerResult:
     logdet_trace: list = field(default_factory=list)
     lnS_trace: list = field(default_factory=list)
     xbar_trace: list = field(default_factory=list)
+    rank_trace: list = field(default_factory=list)
 
 
 def initial_state(sys: UEG):
@@ -367,15 +428,17 @@ def slice_step(sys: UEG, st: WalkerState, x, k, opts: Options, xbar=None):
         xbar = force_bias(sys, st.G) if opts.force_bias else np.zeros(sys.N_alpha, np.complex128)
     B = propagator(sys, x - xbar, opts.exp_order, opts.exact_exp)
     Y, D, T = B @ st.Y, st.D, st.T
+    thr = opts.low_rank
     if opts.stabilise_every > 0 and k % opts.stabilise_every == 0:
-        Y, D, T = stabilise(Y, D, T)
+        Y, D, T = stabilise_truncated(Y, D, T, thr) if thr > 0 else stabilise(Y, D, T)
+    green = (lambda DL, Y, D, T: green_lowrank(DL, Y, D, T, thr)) if thr > 0 else GREEN[opts.green]
     modified = opts.overlap == "modified"
-    Gn, ldn = GREEN[opts.green](left_diagonal(sys, 0 if modified else k), Y, D, T)
+    Gn, ldn = green(left_diagonal(sys, 0 if modified else k), Y, D, T)
     lnS = 2.0 * (ldn - st.logdet)                  # two identical spin blocks
     gauss = np.sum(x * xbar - 0.5 * xbar * xbar)   # Eq. import
     logw, alive = update_weight(st.logw, st.alive, lnS, gauss, opts.constraint)
     if modified and k == sys.n_slices:
-        Gp, ldp = GREEN[opts.green](left_diagonal(sys, k), Y, D, T)
+        Gp, ldp = green(left_diagonal(sys, k), Y, D, T)
         logw, alive = update_weight(logw, alive, 2.0 * (ldp - ldn), 0j, opts.constraint)
         Gn, ldn = Gp, ldp
     return WalkerState(Y, D, T, Gn, ldn, logw, alive), lnS, gauss, xbar
@@ -395,6 +458,7 @@ def propagate_walker(sys: UEG, fields, opts: Options, n_slices=None, record=Fals
             res.logdet_trace.append(st.logdet)
             res.lnS_trace.append(lnS)
             res.xbar_trace.append(xbar)
+            res.rank_trace.append(len(st.D))
     res.logw, res.alive, res.G, res.logdet = st.logw, st.alive, st.G, st.logdet
     if want_estimator:
         res.energy, res.number = local_energy(sys, st.G)
