@@ -75,6 +75,15 @@ typedef struct {
     uint64_t seed;             /* key of the on-device field generator (ftq_fields)       */
     void*    cuda_stream;      /* cudaStream_t the library launches on (NULL = default)  */
     double   force_bias_cap;   /* 0 = off (no cap is applied in this version)             */
+    double   low_rank_threshold; /* 0 = full rank.  > 0: low-rank truncation (Sec.
+                                    "Exploiting the low-rank structure", Eq. thresh) with
+                                    this absolute threshold (the paper uses 1e-6): every
+                                    stabilisation keeps the leading columns of the pivoted
+                                    QR with |R_jj| >= threshold (at least one), the trial
+                                    block keeps its entries >= threshold, and G and
+                                    ln det(I + A) come from the Woodbury identity and the
+                                    matrix determinant lemma in the kept dimensions.
+                                    complex128 path only (FTQ_FP64); FTQ_EINVAL otherwise */
 } ftq_opts;
 
 /* One system of a ragged batch (ftq_init_batch). */
@@ -219,6 +228,12 @@ int ftq_mu_grad(ftq_ctx* ctx, double* out_host, double* per_walker_dev);
  *  Im gauss_k, unused} where gauss_k = x_k.xbar_k - xbar_k.xbar_k / 2 of the
  * last slice (Eq. import). */
 int ftq_weights(ftq_ctx* ctx, double* out_dev);
+
+/* Rank m of every walker's right block (Sec. "Exploiting the low-rank
+ * structure": the number of kept scales after the last stabilisation; M on
+ * the full-rank path).  ranks_host: caller-owned host int[W]; synchronises the
+ * stream. */
+int ftq_ranks(ftq_ctx* ctx, int* ranks_host);
 
 /* Read and clear the latched device status: FTQ_OK, FTQ_ENUMERIC (zero or
  * NaN pivot, non-finite log-determinant) or FTQ_ETIMEOUT (a tensor-core

@@ -27,7 +27,7 @@ class Opts(ctypes.Structure):
                 ("exp_order", ctypes.c_int), ("precision", ctypes.c_int),
                 ("constraint", ctypes.c_int), ("overlap", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
-                ("force_bias_cap", ctypes.c_double)]
+                ("force_bias_cap", ctypes.c_double), ("low_rank_threshold", ctypes.c_double)]
 
 
 class System(ctypes.Structure):
@@ -40,7 +40,7 @@ EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
            "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control", "ftq_structure_factor", "ftq_pair_branch",
-           "ftq_last_error", "ftq_destroy"]
+           "ftq_ranks", "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
            "border": 7, "fields": 8, "population": 9}
 K_COUNT = 10
@@ -68,6 +68,7 @@ def load_library(path=None):
     lib.ftq_estimators.argtypes = [vp, dp, vp]
     lib.ftq_weights.argtypes = [vp, vp]
     lib.ftq_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.ftq_ranks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ftq_query.argtypes = [vp, i, i64p]
     lib.ftq_query_f64.argtypes = [vp, i, dp]
     lib.ftq_basis.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
@@ -103,7 +104,7 @@ class Propagator:
 
     def __init__(self, N, M, rs, theta, dtau, mu=None, walkers=64, stabilise_every=5,
                  exp_order=6, precision=FTQ_FP64, constraint=FTQ_PHASELESS, seed=0, stream=None,
-                 overlap=FTQ_OVERLAP_PAPER):
+                 overlap=FTQ_OVERLAP_PAPER, low_rank=0.0):
         import torch
         if not torch.cuda.is_available():
             raise FTQError("no CUDA device: the propagator has no CPU path")
@@ -111,7 +112,7 @@ class Propagator:
         self.lib = load_library()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         o = Opts(walkers, stabilise_every, exp_order, precision, constraint, overlap, seed,
-                 ctypes.c_void_p(self.stream.cuda_stream), 0.0)
+                 ctypes.c_void_p(self.stream.cuda_stream), 0.0, float(low_rank))
         h = ctypes.c_void_p()
         st = self.lib.ftq_init_ueg(ctypes.byref(h), N, M, rs, theta,
                                    float("nan") if mu is None else float(mu), dtau, ctypes.byref(o))
@@ -271,6 +272,13 @@ class Propagator:
         out = t.empty((self.W, 8), dtype=t.float64, device="cuda")
         self._check(self.lib.ftq_weights(self.h, ctypes.c_void_p(out.data_ptr())), "ftq_weights")
         return out
+
+    def ranks(self):
+        """Rank of every walker's right block (numpy int array [W])."""
+        import numpy as np
+        out = (ctypes.c_int * self.W)()
+        self._check(self.lib.ftq_ranks(self.h, out), "ftq_ranks")
+        return np.array(out[:], dtype=np.int64)
 
     def estimators(self, per_walker=True):
         t = self._torch

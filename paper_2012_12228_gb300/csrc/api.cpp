@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "ftq_internal.h"
 
@@ -70,6 +71,10 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         return fail(nullptr, FTQ_EINVAL, "unknown constraint");
     if (opts->overlap != FTQ_OVERLAP_PAPER && opts->overlap != FTQ_OVERLAP_MODIFIED)
         return fail(nullptr, FTQ_EINVAL, "unknown overlap");
+    if (!(opts->low_rank_threshold >= 0.0) || !std::isfinite(opts->low_rank_threshold))
+        return fail(nullptr, FTQ_EINVAL, "low_rank_threshold must be finite and >= 0");
+    if (opts->low_rank_threshold > 0.0 && opts->precision != FTQ_FP64)
+        return fail(nullptr, FTQ_EINVAL, "low-rank truncation runs on the complex128 path (FTQ_FP64)");
     if (N % 2 != 0) return fail(nullptr, FTQ_EINVAL, "N must be even (unpolarised gas)");
     ftq_ctx* c = new (std::nothrow) ftq_ctx();
     if (!c) return fail(nullptr, FTQ_ENOMEM, "host allocation failed");
@@ -315,6 +320,17 @@ int ftq_weights(ftq_ctx* c, double* out_dev) {
     cudaError_t e = cudaMemcpy2DAsync(out_dev, sizeof(double) * 8, c->wstate, sizeof(double) * ftq::WSTRIDE,
                                       sizeof(double) * 8, c->W, cudaMemcpyDeviceToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "weights");
+    return FTQ_OK;
+}
+
+int ftq_ranks(ftq_ctx* c, int* ranks_host) {
+    if (!c || !ranks_host) return fail(c, FTQ_EINVAL, "NULL argument");
+    std::vector<double> r((size_t)c->W);
+    cudaError_t e = cudaMemcpy2DAsync(r.data(), sizeof(double), c->wstate + 12, sizeof(double) * ftq::WSTRIDE,
+                                      sizeof(double), c->W, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ranks");
+    for (int w = 0; w < c->W; ++w) ranks_host[w] = (int)r[(size_t)w];
     return FTQ_OK;
 }
 

@@ -5,6 +5,7 @@
 // for the factorisations; tiled batched GEMM for the chain.
 #include <cmath>
 
+#include "block_reduce.cuh"
 #include "complex_math.cuh"
 #include "ftq_internal.h"
 
@@ -12,50 +13,6 @@ namespace ftq {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-
-// ---------------------------------------------------------------- reductions
-template <typename T>
-__device__ T block_sum(T v, T* sh) {
-    // deterministic: fixed shuffle tree then fixed order over warps
-    for (int o = 16; o > 0; o >>= 1) v = v + shfl_down(v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        T acc = sh[0];
-        for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i) acc = acc + sh[i];
-        sh[0] = acc;
-    }
-    __syncthreads();
-    T r = sh[0];
-    __syncthreads();
-    return r;
-}
-
-// argmax of val over the block; ties go to the lowest index.
-__device__ int block_argmax(double val, int idx, double* shv, int* shi) {
-    for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, val, o);
-        int oi = __shfl_down_sync(0xffffffffu, idx, o);
-        if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) { shv[wid] = val; shi[wid] = idx; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double bv = shv[0];
-        int bi = shi[0];
-        for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i)
-            if (shv[i] > bv || (shv[i] == bv && shi[i] < bi)) { bv = shv[i]; bi = shi[i]; }
-        shi[0] = bi;
-    }
-    __syncthreads();
-    int r = shi[0];
-    __syncthreads();
-    return r;
-}
 
 // ---------------------------------------------------------------- init
 __global__ void k_init_matrices(double2* Y, double2* Tinv, double2* G, const double* g0, int M, long total) {
@@ -77,6 +34,7 @@ __global__ void k_init_walkers(double2* DR, double* ws, int M, int W, double ld0
         for (int q = 0; q < WSTRIDE; ++q) s[q] = 0.0;
         s[2] = 1.0;
         s[3] = ld0;
+        s[12] = (double)M;
     }
 }
 
@@ -143,12 +101,15 @@ __global__ void __launch_bounds__(256) k_chain_step(const double2* __restrict__ 
                                                    double2* __restrict__ out, const double2* __restrict__ phi,
                                                    const uint16_t* __restrict__ vidx, const double* __restrict__ zs,
                                                    const double* __restrict__ us, const double* __restrict__ os,
-                                                   double alpha, int M, int nslot, int tiles) {
+                                                   double alpha, int M, int nslot, int tiles,
+                                                   const double* __restrict__ rank_ws) {
     __shared__ double2 As[CK][CT + 1];
     __shared__ double2 Bs[CK][CT + 1];
     const int w = blockIdx.y;
     const int ti = blockIdx.x / tiles, tj = blockIdx.x % tiles;
     const int r0 = ti * CT, c0 = tj * CT;
+    // low rank: only the first m columns of the chain are live
+    if (rank_ws && c0 >= (int)rank_ws[(long)WSTRIDE * w + 12]) return;
     const long off = (long)w * M * M;
     const double2* Z = Zin + off;
     const double2* ph = phi + (long)w * nslot;
@@ -622,7 +583,8 @@ cudaError_t launch_chain(ftq_ctx* c) {
         LaunchScope ls(c, FTQ_K_CHAIN);
         k_chain_step<<<grid, 256, 0, c->stream>>>(zin, c->Y, out, c->phi, c->tab.vidx,
                                                   j == p ? c->tab.h : nullptr, c->tab.h,
-                                                  j == 1 ? c->tab.h : nullptr, 1.0 / j, M, c->nslot, tiles);
+                                                  j == 1 ? c->tab.h : nullptr, 1.0 / j, M, c->nslot, tiles,
+                                                  c->opts.low_rank_threshold > 0.0 ? c->wstate : nullptr);
         zin = out;
         cur ^= 1;
     }
@@ -645,6 +607,7 @@ cudaError_t launch_qrcp64(ftq_ctx* c, const double2* Yin, double2* Qout) {
 
 cudaError_t launch_qrcp(ftq_ctx* c) {
     if (c->opts.precision != FTQ_FP64) return mixed_qrcp(c);
+    if (c->opts.low_rank_threshold > 0.0) return launch_qrcp_lr(c);
     cudaError_t e = launch_qrcp64(c, c->Y, c->zbuf[0]);
     double2* q = c->zbuf[0];
     c->zbuf[0] = c->Y;
@@ -661,6 +624,7 @@ cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update, boo
     const int M = c->M;
     size_t sm = (2 * sizeof(double2) + 3 * sizeof(double) + sizeof(int)) * M;
     int nt = fact_threads(M);
+    if (c->opts.low_rank_threshold > 0.0) return launch_green_lr(c, Y, k, update, physical);
     const double lscale = physical ? 0.0 : left_scale(c, k);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     LaunchScope ls(c, FTQ_K_GREEN);

@@ -14,7 +14,7 @@ namespace ftq {
 //   [0] ln|w|  [1] arg w  [2] alive  [3] Re ln det(I+A)  [4] Im ln det
 //   [5] Re gauss_k  [6] Im gauss_k  [7] parity of det T
 //   [8] d ln|w|/dmu  [9] Re t_k  [10] Im t_k  (t_k = d ln det(I+A_k)/dmu)
-//   [11] d arg w/dmu  [12..15] unused
+//   [11] d arg w/dmu  [12] rank m of the right block (M at full rank)  [13..15] unused
 // The per-walker estimator record uses the same stride:
 //   [0..2] as above, [3] Re E, [4] Im E, [5] Re N, [6] Im N, [7] unused,
 //   [8] d ln|w|/dmu, [9] d arg w/dmu, [10] Re dE, [11] Im dE, [12] Re dN, [13] Im dN
@@ -195,6 +195,9 @@ cudaError_t launch_green64(ftq_ctx* c, const double2* Y, int k, bool update_weig
 // dtau times the power of B_T in the trial block at slice k: n - k for the
 // overlap of Eq. ftoratio, n for the modified overlap of Eq. ztfix.
 double left_scale(const ftq_ctx* c, int k);
+// Low-rank truncation of the complex128 path (lowrank.cu).
+cudaError_t launch_qrcp_lr(ftq_ctx* c);
+cudaError_t launch_green_lr(ftq_ctx* c, const double2* Y, int k, bool update_weights, bool physical);
 cudaError_t launch_force_bias_any(ftq_ctx* c, const double* x, const void* G, bool g32);
 
 // Mixed-precision launchers (mixed_kernels.cu).
