@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -51,6 +53,9 @@ def parse():
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--walkers", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lowrank", action="store_true",
+                    help="add the low-rank truncation measurement (complex128, N=14, M=515, r_s=0.5, Theta=0.125)")
+    ap.add_argument("--lowrank-walkers", type=int, default=152)
     ap.add_argument("--oracle-sample", nargs=2, type=int, default=None, metavar=("WALKERS", "SLICES"),
                     help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -364,6 +369,59 @@ def measure_ragged(ftq, torch, dev, steps=4, warmup=3):
     return res
 
 
+LOWRANK = dict(N=14, M=515, rs=0.5, theta=0.125, dtau=0.05, seed=1240)
+
+
+def measure_lowrank(ftq, torch, dev, W, thr=1e-6):
+    """Whole-path complex128 throughput with and without low-rank truncation
+    (threshold 1e-6) on a system with M >> N-bar at low temperature (N = 14,
+    M = 515, r_s = 0.5, Theta = 0.125, dtau = 0.05: 22 slices), the same
+    fields for both, plus the kept ranks along the path: m_R of the right
+    block after every stabilisation (ftq_ranks) and m_L of the trial block."""
+    c = LOWRANK
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for t in (0.0, thr):
+        p = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, stabilise_every=5,
+                           exp_order=6, precision=ftq.FTQ_FP64, stream=stream, low_rank=t)
+        n, na = p.n_slices, p.n_alpha
+        f = torch.from_numpy(gaussian_fields(c["seed"], n, W, na)).to(dev)
+        p.propagate(f[:1].contiguous())          # warm-up (first launches, shared-memory attributes)
+        p.reset()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p.propagate(f)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        est = p.estimators(per_walker=True)
+        pw = est["per_walker"].cpu().numpy()
+        alive = pw[:, 2] > 0.5
+        out = {"value": W * n / (ms / 1e3), "unit": "walker-slices/s", "ms_path": ms,
+               "E_per_electron": float(np.mean(pw[alive, 3]) / c["N"]), "N": float(np.mean(pw[alive, 5])),
+               "alive": int(alive.sum()), "status": p.status()}
+        if t > 0:
+            trace = []
+            p.reset()
+            for k0 in range(0, n, 5):
+                p.propagate(f[k0:min(k0 + 5, n)].contiguous())
+                trace.append(int(np.max(p.ranks())))
+            L, mu_t, dt = p.query_f64("L"), p.query_f64("MU_T"), p.query_f64("DTAU")
+            eps = 0.5 * (2 * np.pi / L) ** 2 * np.sum(np.array(p.basis(), dtype=np.float64) ** 2, axis=1)
+            m_left = [int(np.sum(np.exp(-(n - k) * dt * (eps - mu_t)) >= t)) for k in range(5, n + 1, 5)]
+            out.update({"threshold": t, "m_R_max_after_each_stabilisation": trace,
+                        "m_L_at_each_stabilisation": m_left})
+        res["low_rank" if t > 0 else "full_rank"] = out
+        p.close()
+    res.update({"workload": "ueg_n14_m515 (r_s=0.5, Theta=0.125, dtau=0.05)", "M": c["M"], "walkers": W,
+                "n_slices": n, "precision": "c128",
+                "speedup": res["low_rank"]["value"] / res["full_rank"]["value"],
+                "E_per_electron_abs_diff": abs(res["low_rank"]["E_per_electron"] - res["full_rank"]["E_per_electron"]),
+                "N_abs_diff": abs(res["low_rank"]["N"] - res["full_rank"]["N"])})
+    return res
+
+
 def accuracy_vs_fp64(ftq, torch, dev, W=32):
     """E/N at tau = beta of the mixed and the complex128 path on identical
     fields (whole path, W walkers)."""
@@ -424,6 +482,7 @@ def run_ours(args, rank, world, local_rank):
     acc = None
     if args.precision == "mixed" and not args.no_accuracy and rank == 0:
         acc = accuracy_vs_fp64(ftq, torch, dev)
+    lowrank = measure_lowrank(ftq, torch, dev, args.lowrank_walkers) if args.lowrank and rank == 0 else None
     ragged = None
     if args.precision == "mixed" and not args.no_ragged and rank == 0:
         ragged = measure_ragged(ftq, torch, dev)
@@ -461,6 +520,8 @@ def run_ours(args, rank, world, local_rank):
         line["error_vs_fp64"] = acc
     if ragged:
         line["ragged_batch"] = ragged
+    if lowrank:
+        line["low_rank"] = lowrank
     if head.get("autotune"):
         line["config"]["autotune"] = head["autotune"]
     if world == 1 and not args.no_cpu_baseline:
