@@ -482,8 +482,10 @@ __device__ __forceinline__ float2 warp_sum(float2 v) {
 }
 
 // One warp per output entry, lanes over the contraction index (coalesced
-// reads of the chain rows), V from the shared difference cube.
-__global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ Zin, const float* __restrict__ Yu,
+// reads of the chain rows), V from the shared difference cube.  Eight blocks
+// per SM (at most 32 registers) keep 1024 walkers in one wave, and two
+// partial sums per lane keep eight chain loads in flight.
+__global__ void __launch_bounds__(256, 8) k_chain_border(const float* __restrict__ Zin, const float* __restrict__ Yu,
                                                      float* __restrict__ out, const double2* __restrict__ phi,
                                                      const int* __restrict__ pk, const uint16_t* __restrict__ qcube,
                                                      const double* __restrict__ zs, const double* __restrict__ us,
@@ -516,9 +518,15 @@ __global__ void __launch_bounds__(256) k_chain_border(const float* __restrict__ 
         }
         __syncthreads();
         for (int c = warp; c < M; c += nw) {
-            float2 acc = make_float2(0.f, 0.f);
-            for (int k = lane; k < M; k += 32) acc = cfma(vec[k], P.load(Z, k, c), acc);
-            acc = warp_sum(acc);
+            float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
+            int k = lane;
+            for (; k + 32 < M; k += 64) {
+                const float2 z0 = P.load(Z, k, c), z1 = P.load(Z, k + 32, c);
+                acc = cfma(vec[k], z0, acc);
+                acc2 = cfma(vec[k + 32], z1, acc2);
+            }
+            if (k < M) acc = cfma(vec[k], P.load(Z, k, c), acc);
+            acc = warp_sum(acc + acc2);
             if (lane == 0) border_store(O, U, P, us, os, alpha, i, c, acc);
         }
         __syncthreads();
