@@ -259,6 +259,9 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     t_ms = max_over_ranks(e0.elapsed_time(e1))
     out["ms_per_step"] = t_ms / steps
     out["value"] = world * W * stab * steps / (t_ms / 1e3)
+    if world > 1:                   # weighted estimate over the walkers of every replica
+        from paper_2012_12228_gb300 import replicas
+        est = replicas.combine_estimates(est, device=dev)
     out["estimate"] = {"E_per_electron": est["E"].real / c["N"], "N": est["N"].real, "alive": est["n_alive"]}
 
     if with_e2e:
@@ -465,13 +468,10 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
+    from paper_2012_12228_gb300 import replicas
+
     def max_over_ranks(x):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return replicas.max_over_ranks(x, device=dev) if world > 1 else x
 
     head = measure_path(ftq, torch, dev, args.precision, W, args.steps, args.warmup, world, rank, barrier,
                         max_over_ranks, with_e2e=True, with_clocks=True)
