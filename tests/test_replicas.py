@@ -80,3 +80,23 @@ def test_two_rank_combination_equals_union(case):
         assert abs(comb["sum_w"] - ref["sum_w"]) < 1e-12 * abs(ref["sum_w"])
         assert abs(comb["E"] - E_ref) < 1e-12 * abs(E_ref)
         assert abs(comb["N"] - N_ref) < 1e-12 * abs(N_ref)
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """bench.py --impl reference under torchrun with two CPU ranks: rank 0
+    alone times the oracle sample and prints the JSON line; rank 1 exits 0."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()),
+           os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=root, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
