@@ -122,3 +122,56 @@ def test_rejected_with_mixed_precision(ftq):
         make(ftq, "ueg_n2_m7", 4, precision=ftq.FTQ_MIXED, low_rank=1e-6)
     with pytest.raises(ftq.FTQError):
         make(ftq, "ueg_n2_m7", 4, low_rank=-1.0)
+
+
+def test_mu_derivative_with_low_rank(ftq):
+    """Per-walker mu derivatives along a truncated path (the trial block
+    keeps fewer than its 7 entries early on) against the oracle's central
+    differences."""
+    c = WORKLOADS["ueg_n2_m7"]
+    s = UEG(c["N"], c["M"], c["rs"], c["theta"], c["dtau"])
+    W, thr = 16, 0.05
+    assert np.sum(afqmc.left_diagonal(s, 1) >= thr) < s.M
+    f = gaussian_fields(c["seed"] + 63, s.n_slices, W, s.N_alpha)
+    p = make(ftq, "ueg_n2_m7", W, low_rank=thr)
+    p.propagate(torch.from_numpy(f).cuda())
+    pw = p.mu_grad()["per_walker"].cpu().numpy()
+    p.close()
+    fd = afqmc.mu_derivative_walkers_fd(s, f, afqmc.Options(low_rank=thr))
+    checked = 0
+    for w in range(W):
+        if not fd[w]["alive"]:
+            continue
+        checked += 1
+        assert abs(pw[w, 0] - fd[w]["dlogw"]) < 1e-6 * max(1, abs(fd[w]["dlogw"]))
+        assert abs(pw[w, 2] - fd[w]["dE"].real) < 1e-6 * max(1, abs(fd[w]["dE"]))
+        assert abs(pw[w, 4] - fd[w]["dN"].real) < 1e-6 * max(1, abs(fd[w]["dN"]))
+    assert checked >= W // 2
+
+
+def test_population_control_with_low_rank(ftq):
+    """Combs between truncated slices copy the whole walker state, rank
+    included: the path equals the oracle's comb path."""
+    from oracle.population import run_with_population_control
+    c = WORKLOADS["ueg_n14_m57"]
+    s = UEG(c["N"], c["M"], c["rs"], c["theta"], c["dtau"])
+    W, thr = 16, 1e-3
+    f = gaussian_fields(c["seed"] + 64, s.n_slices, W, s.N_alpha)
+    ref = run_with_population_control(s, f, pc_after={40, 60}, xis=(0.3, 0.71), opts=afqmc.Options(low_rank=thr))
+    p = make(ftq, "ueg_n14_m57", W, low_rank=thr)
+    fd = torch.from_numpy(f).cuda()
+    p.propagate(fd[:40].contiguous())
+    p.population_control(0.3)
+    p.propagate(fd[40:60].contiguous())
+    p.population_control(0.71)
+    p.propagate(fd[60:].contiguous())
+    G = p.green().cpu().numpy()
+    ws = p.weights().cpu().numpy()
+    assert list(p.ranks()) == [len(r.D) for r in ref]
+    for w in range(W):
+        assert np.abs(G[w] - ref[w].G).max() < 1e-9 * np.abs(ref[w].G).max()
+        assert bool(ws[w, 2] > 0.5) == ref[w].alive
+        if ref[w].alive:
+            assert abs(ws[w, 0] - ref[w].logw.real) < 1e-9 * max(1.0, abs(ref[w].logw.real))
+    assert p.status() == 0
+    p.close()

@@ -99,3 +99,27 @@ def test_mixed_matches_fp64(ftq):
     assert np.abs(Ga[alive] - Gb[alive]).max() < 1e-5 * np.abs(Ga).max()
     assert np.max(np.abs(wa[alive, 0] - wb[alive, 0])) < 1e-5 * max(1.0, np.max(np.abs(wa[alive, 0])))
     assert np.max(np.abs(ea[alive, 3] - eb[alive, 3])) < 1e-5 * np.max(np.abs(ea[alive, 3]))
+
+
+def test_mu_derivative_with_modified_overlap(ftq):
+    """d ln|w|/dmu, dE_L/dmu, dN_L/dmu per walker (fixed draws, frozen force
+    bias) against the oracle's central differences along the modified path,
+    the final ratio r included."""
+    c = WORKLOADS["ueg_n2_m7"]
+    s = UEG(c["N"], c["M"], c["rs"], c["theta"], c["dtau"])
+    W = 16
+    f = gaussian_fields(c["seed"] + 43, s.n_slices, W, s.N_alpha)
+    p = make(ftq, "ueg_n2_m7", W)
+    p.propagate(torch.from_numpy(f).cuda())
+    pw = p.mu_grad()["per_walker"].cpu().numpy()
+    p.close()
+    fd = afqmc.mu_derivative_walkers_fd(s, f, afqmc.Options(overlap="modified"))
+    checked = 0
+    for w in range(W):
+        if not fd[w]["alive"]:
+            continue
+        checked += 1
+        assert abs(pw[w, 0] - fd[w]["dlogw"]) < 1e-6 * max(1, abs(fd[w]["dlogw"]))
+        assert abs(pw[w, 2] - fd[w]["dE"].real) < 1e-6 * max(1, abs(fd[w]["dE"]))
+        assert abs(pw[w, 4] - fd[w]["dN"].real) < 1e-6 * max(1, abs(fd[w]["dN"]))
+    assert checked >= W // 2
