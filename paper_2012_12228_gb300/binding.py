@@ -100,7 +100,10 @@ def load_library(path=None):
 class Propagator:
     """One UEG system with W walkers on the current CUDA device.
 
-    Parameters mirror ftq_init_ueg; ``mu=None`` selects mu = mu_T."""
+    Parameters mirror ftq_init_ueg and ftq_opts; ``mu=None`` selects
+    mu = mu_T; ``overlap`` is FTQ_OVERLAP_PAPER (S_k, Eq. ftoratio) or
+    FTQ_OVERLAP_MODIFIED (S~_k, Eq. ztfix); ``low_rank`` > 0 is the
+    truncation threshold of Eq. thresh (complex128 path only)."""
 
     def __init__(self, N, M, rs, theta, dtau, mu=None, walkers=64, stabilise_every=5,
                  exp_order=6, precision=FTQ_FP64, constraint=FTQ_PHASELESS, seed=0, stream=None,
