@@ -64,3 +64,32 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of ftq_opts and ftq_system have the C layout: sizes
+    and every field offset, from a small C program compiled against
+    include/ftq.h."""
+    import shutil
+    import subprocess
+    from paper_2012_12228_gb300.binding import Opts, System
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    prog = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ftq.h"', "int main(void) {"]
+    for cname, cls in (("ftq_opts", Opts), ("ftq_system", System)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, str(prog), "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
+                    "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, cls in (("ftq_opts", Opts), ("ftq_system", System)):
+        assert got[(cname, "size")] == ctypes.sizeof(cls)
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
