@@ -126,3 +126,18 @@ def test_paper_threshold_accuracy_and_compression():
         assert abs(a.number - b.number) < 1e-5 * abs(a.number)
         assert np.abs(a.G - b.G).max() < 1e-5
         assert b.rank_trace[0] == s.M and b.rank_trace[-1] < 0.7 * s.M
+
+
+def test_untruncated_modified_overlap_equals_full_rank():
+    """The low-rank Green's function also serves the modified overlap (trial
+    block B_T^n at every slice, physical G(beta) and the final ratio): with a
+    threshold below every scale it reproduces the full-rank modified path."""
+    s = UEG(2, 7, 1.0, 0.5, 0.05)
+    f = gaussian_fields(56, s.n_slices, 3, s.N_alpha)
+    for constraint in ("phaseless", "free"):
+        a = afqmc.run(s, f, afqmc.Options(overlap="modified", constraint=constraint, green="two_sided"))
+        b = afqmc.run(s, f, afqmc.Options(overlap="modified", constraint=constraint, low_rank=1e-300))
+        for x, y in zip(a, b):
+            assert np.abs(x.G - y.G).max() < 1e-10 * np.abs(x.G).max()
+            assert abs(x.logw.real - y.logw.real) < 1e-9 * max(1.0, abs(x.logw.real))
+            assert abs(wrap(x.logw.imag - y.logw.imag)) < 1e-9
