@@ -417,12 +417,40 @@ def measure_lowrank(ftq, torch, dev, W, thr=1e-6):
                         "m_L_at_each_stabilisation": m_left})
         res["low_rank" if t > 0 else "full_rank"] = out
         p.close()
+    res["compression"] = [compression_trace(ftq, torch, dev, stream, t_, thr)
+                          for t_ in (0.125, 0.5)]
     res.update({"workload": "ueg_n14_m515 (r_s=0.5, Theta=0.125, dtau=0.05)", "M": c["M"], "walkers": W,
                 "n_slices": n, "precision": "c128",
                 "speedup": res["low_rank"]["value"] / res["full_rank"]["value"],
                 "E_per_electron_abs_diff": abs(res["low_rank"]["E_per_electron"] - res["full_rank"]["E_per_electron"]),
                 "N_abs_diff": abs(res["low_rank"]["N"] - res["full_rank"]["N"])})
     return res
+
+
+def compression_trace(ftq, torch, dev, stream, theta, thr, W=16, dtau=0.01):
+    """Ranks along the path of N = 14, M = 515, r_s = 0.5 at temperature
+    Theta (dtau = 0.01): m_R (largest over the walkers) after every
+    stabilisation, m_L of the trial block and m_T = min(m_R, m_L) at the same
+    slices, and the compression 1 - m/M of each (the quantities of the
+    paper's low-rank compression figure)."""
+    c = LOWRANK
+    p = ftq.Propagator(c["N"], c["M"], c["rs"], theta, dtau, walkers=W, stabilise_every=5, exp_order=6,
+                       precision=ftq.FTQ_FP64, stream=stream, low_rank=thr)
+    n, na, M = p.n_slices, p.n_alpha, p.M
+    f = torch.from_numpy(gaussian_fields(c["seed"] + 1, n, W, na)).to(dev)
+    L, mu_t, dt = p.query_f64("L"), p.query_f64("MU_T"), p.query_f64("DTAU")
+    eps = 0.5 * (2 * np.pi / L) ** 2 * np.sum(np.array(p.basis(), dtype=np.float64) ** 2, axis=1)
+    rows = []
+    for k0 in range(0, n - n % 5, 5):
+        p.propagate(f[k0:k0 + 5].contiguous())
+        k = k0 + 5
+        m_r = int(np.max(p.ranks()))
+        m_l = int(np.sum(np.exp(-(n - k) * dt * (eps - mu_t)) >= thr))
+        rows.append({"tau": k * dt, "m_R": m_r, "m_L": m_l, "m_T": min(m_r, m_l)})
+    status = p.status()
+    p.close()
+    return {"theta": theta, "dtau": dt, "n_slices": n, "walkers": W, "status": status, "trace": rows,
+            "mean_compression_T": float(np.mean([1.0 - r["m_T"] / M for r in rows]))}
 
 
 def accuracy_vs_fp64(ftq, torch, dev, W=32):
