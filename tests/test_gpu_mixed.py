@@ -7,7 +7,7 @@ hi + lo tf32 pairs (relative error <= 2^-22 = 2.4e-7 per rounding) and the
 per-slice LU runs in FP32 (unit roundoff 6e-8 times the growth of a
 well-conditioned, pivoted M x M system); a path of n slices accumulates
 these, so G(beta) is held to 1e-4 relative and the weighted energy per
-electron to the benchmark spec's bound of 1e-5 Ha.
+electron to the mixed-precision accuracy bound of 1e-5 Ha.
 """
 import math
 
