@@ -24,6 +24,7 @@ namespace ftq {
 namespace {
 
 constexpr int QP = 32;   // columns per Q panel
+constexpr int NBJ = 2;   // columns per block of the T^-1 update
 
 __device__ double bsum_d(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -82,7 +83,8 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
                               double* __restrict__ ws,
                               int* __restrict__ status, int M, Planes P, size_t wstride) {
     extern __shared__ unsigned char smem_raw[];
-    double* cn = reinterpret_cast<double*>(smem_raw);      // [M] column norms of C
+    double* ub = reinterpret_cast<double*>(smem_raw);      // [M][NBJ][3] U block of the T^-1 update
+    double* cn = ub + 3 * NBJ * M;                         // [M] column norms of C
     int* perm = reinterpret_cast<int*>(cn + M);            // [M] C Pi column j = C column perm[j]
     unsigned char* seen = reinterpret_cast<unsigned char*>(perm + M);   // [M]
     __shared__ double shd[32];
@@ -226,29 +228,70 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
         }
     }
     __syncthreads();
-    // T^-1 <- T^-1[:, perm] U^-1, one row per thread (XT column-major).  The
-    // complex sums over m use three real products per term (sum ac, sum bd,
-    // sum (a + b)(c + d): the three-multiplication complex product), with
-    // a + b of X kept beside X and c + d of U precomputed above.
+    // T^-1 <- T^-1[:, perm] U^-1, one row per thread (XT column-major), in
+    // blocks of NBJ columns: the block's entries of U (Re, Im and Re + Im) for
+    // every earlier row m are staged in shared memory, so that each X[i][m]
+    // read from memory serves NBJ columns.  The complex sums over m use three
+    // real products per term (sum ac, sum bd, sum (a + b)(c + d): the
+    // three-multiplication complex product), with a + b of X kept beside X
+    // and c + d of U precomputed above; every column sums m = 0 .. j - 1 in
+    // order, as the column-by-column solve does.
     double* XS = xsum + off;
-    for (int i = tid; i < M; i += nt) {
-        for (int j = 0; j < M; ++j) {
-            double pr = 0.0, qr = 0.0, rr = 0.0;
-            for (int m = 0; m < j; ++m) {
-                const double2 x = XT[(long)m * M + i];
+    for (int jb = 0; jb < M; jb += NBJ) {
+        const int nb = min(NBJ, M - jb);
+        for (int e = tid; e < (jb + nb) * NBJ; e += nt) {
+            const int m = e / NBJ, q = e % NBJ, j = jb + q;
+            double ur = 0.0, ui = 0.0, us = 0.0;
+            if (q < nb && m < j) {
                 const double2 u = C[(long)m * M + j];
-                pr = fma(x.x, u.x, pr);
-                qr = fma(x.y, u.y, qr);
-                rr = fma(XS[(long)m * M + i], C[(long)j * M + m].x, rr);
+                ur = u.x;
+                ui = u.y;
+                us = C[(long)j * M + m].x;
             }
-            double2 s = Ti[(long)i * M + perm[j]];
-            s.x -= pr - qr;
-            s.y -= rr - pr - qr;
-            XT[(long)j * M + i] = s;
-            XS[(long)j * M + i] = s.x + s.y;
+            ub[3 * e] = ur;
+            ub[3 * e + 1] = ui;
+            ub[3 * e + 2] = us;
         }
-        for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
+        __syncthreads();
+        for (int i = tid; i < M; i += nt) {
+            double pr[NBJ], qr[NBJ], rr[NBJ];
+#pragma unroll
+            for (int q = 0; q < NBJ; ++q) pr[q] = qr[q] = rr[q] = 0.0;
+            for (int m = 0; m < jb; ++m) {
+                const double2 x = XT[(long)m * M + i];
+                const double xs = XS[(long)m * M + i];
+                const double* u = ub + 3 * NBJ * m;
+#pragma unroll
+                for (int q = 0; q < NBJ; ++q) {
+                    pr[q] = fma(x.x, u[3 * q], pr[q]);
+                    qr[q] = fma(x.y, u[3 * q + 1], qr[q]);
+                    rr[q] = fma(xs, u[3 * q + 2], rr[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NBJ; ++q) {
+                if (q < nb) {
+                    const int j = jb + q;
+                    for (int q2 = 0; q2 < q; ++q2) {          // m = jb + q2, solved above
+                        const long o = (long)(jb + q2) * M + i;
+                        const double2 x = XT[o];
+                        const double* u = ub + 3 * (NBJ * (jb + q2) + q);
+                        pr[q] = fma(x.x, u[0], pr[q]);
+                        qr[q] = fma(x.y, u[1], qr[q]);
+                        rr[q] = fma(XS[o], u[2], rr[q]);
+                    }
+                    double2 s = Ti[(long)i * M + perm[j]];
+                    s.x -= pr[q] - qr[q];
+                    s.y -= rr[q] - pr[q] - qr[q];
+                    XT[(long)j * M + i] = s;
+                    XS[(long)j * M + i] = s.x + s.y;
+                }
+            }
+        }
+        __syncthreads();
     }
+    for (int i = tid; i < M; i += nt)
+        for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
     if (tid == 0) {
         double* st = ws + (long)WSTRIDE * w;
         st[7] = (double)(((int)st[7]) ^ parity);
@@ -331,8 +374,14 @@ cudaError_t launch_qr_prepiv(ftq_ctx* c) {
     P.part = (size_t)c->LD * 2 * c->Kp;
     const size_t ws = 2 * P.part;
     int nt = (M + 31) / 32 * 32;
-    nt = nt < 64 ? 64 : (nt > 1024 ? 1024 : nt);
-    const size_t sm1 = (sizeof(double) + sizeof(int) + 1) * M + 16;
+    nt = nt < 64 ? 64 : (nt > 288 ? 288 : nt);          // the launch bound; every loop strides by nt
+    const size_t sm1 = (3 * NBJ + 1) * sizeof(double) * M + (sizeof(int) + 1) * M + 16;
+    static size_t sm1_set = 48 * 1024;
+    if (sm1 > sm1_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_qr_prepiv64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+        if (e != cudaSuccess) return e;
+        sm1_set = sm1;
+    }
     {
         LaunchScope ls(c, FTQ_K_QRCP);
         k_qr_prepiv64<<<c->W, nt, sm1, c->stream>>>(c->Ypl, c->work, c->work2, c->DR, c->Tinv, c->w2_32, c->htau,
