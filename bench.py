@@ -163,7 +163,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TRAFFIC_PER_WALKER = {
     ("mixed", "green"): (1.054e9 / 128, "profiles/green32b_ueg_n66_m257_w128.md"),
     ("mixed", "chain"): (0.3198e9 / 128, "profiles/chain_tc_ueg_n66_m257_w128.md"),
-    ("mixed", "qrcp"): (29.386e9 / 128, "profiles/qr_prepiv64_ueg_n66_m257_w128.md"),
+    ("mixed", "qrcp"): (20.199e9 / 128, "profiles/qr_prepiv64_ueg_n66_m257_w128.md"),
     ("fp64", "chain"): (0.3867e9 / 128, "profiles/chain_fp64_ueg_n66_m257_w128.md"),
 }
 
