@@ -89,12 +89,17 @@ def run_oracle_child(walkers, slices, threads):
 
 
 def cpu_baseline(walkers=6, slices=5):
+    """The oracle on a bounded sample of the workload, with all host cores
+    and, beside it, with one BLAS thread (one walker)."""
     cores = os.cpu_count() or 1
     res = run_oracle_child(walkers, slices, cores)
+    one = run_oracle_child(1, slices, 1)
     return {"value": res["walker_slices"] / res["seconds"], "unit": "walker-slices/s", "cores": cores,
             "kind": "oracle",
             "sample": f"{walkers} walkers x {slices} slices (one stabilisation block) of {WORKLOAD}, "
-                      f"{res['seconds']:.1f} s, NumPy/SciPy BLAS threads = {cores}"}
+                      f"{res['seconds']:.1f} s, NumPy/SciPy BLAS threads = {cores}",
+            "one_core": {"value": one["walker_slices"] / one["seconds"], "cores": 1,
+                         "sample": f"1 walker x {slices} slices, {one['seconds']:.1f} s, BLAS threads = 1"}}
 
 
 # ---------------------------------------------------------------- clocks
