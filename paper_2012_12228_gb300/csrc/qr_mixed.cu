@@ -109,7 +109,14 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
             float2 y = P.load(Yw, i, c);
             s += (double)y.x * y.x + (double)y.y * y.y;
         }
-        cn[c] = s * abs2(Dw[c]);
+        double v = s * abs2(Dw[c]);
+        // a NaN norm would compare false both ways and give two columns one
+        // rank (leaving an entry of perm unset); rank it last and latch
+        if (v != v) {
+            v = -INFINITY;
+            atomicOr(status, 1);
+        }
+        cn[c] = v;
     }
     __syncthreads();
     for (int c = tid; c < M; c += nt) {
