@@ -33,7 +33,8 @@ F  The printed stable-G formula transposes the wrong factors; the
 I  exp(V) is a Taylor series of order p (default 6); Pade expm is reported
    beside it as the truncation error.
 K  theta_k = arg S_k evaluated on the shifted fields; a walker with
-   cos(theta_k) <= 0 is killed (weight 0) and stays dead.
+   cos(theta_k) <= 0 is killed (weight 0) and stays dead, and so is a walker
+   whose ratio or Gaussian factor is not finite (the paper is silent there).
 L  Estimates are taken at tau = beta; sum_w w Re(eps) / sum_w w.
 M  B uses mu, B_T uses mu_T.
 
@@ -404,11 +405,15 @@ def initial_state(sys: UEG):
 
 def update_weight(logw, alive, lnS, gauss, constraint):
     """w <- |I| max(0, cos theta) with I = S e^gauss, theta = arg S (Eqs.
-    import, phimport, theta; reading K), or w <- w I in free projection."""
+    import, phimport, theta; reading K), or w <- w I in free projection.
+    A phaseless walker whose ratio or Gaussian factor is not finite is
+    dropped (weight 0; the paper is silent on non-finite ratios)."""
     if constraint == "free":
         return logw + lnS + gauss, alive
     if alive:
         c = math.cos(lnS.imag)                      # theta_k = arg S_k
+        if not (math.isfinite(lnS.real + gauss.real) and math.isfinite(c)):
+            return logw, False
         if c <= 0.0:
             return logw, False
         return logw + lnS.real + gauss.real + math.log(c), alive
@@ -486,9 +491,10 @@ def weighted_estimate(results, constraint="phaseless"):
         ref = np.max(lw.real)
         w = np.exp(lw - ref)
         return np.sum(w * E) / np.sum(w), np.sum(w * Nn) / np.sum(w), np.sum(w)
-    lwr = np.where(alive, lw.real, -np.inf)
+    ok = alive & np.isfinite(lw.real)               # a non-finite ln|w| weighs 0
+    lwr = np.where(ok, lw.real, -np.inf)
     ref = np.max(lwr)
-    w = np.where(alive, np.exp(lwr - ref), 0.0)
+    w = np.where(ok, np.exp(lwr - ref), 0.0)
     return np.sum(w * E.real) / np.sum(w), np.sum(w * Nn.real) / np.sum(w), np.sum(w)
 
 

@@ -34,16 +34,19 @@ from .afqmc import Options, initial_state, slice_step
 
 
 def comb_counts(weights, xi):
-    """Copies n_i of every walker for the comb with draw xi (sums in index order)."""
+    """Copies n_i of every walker for the comb with draw xi (sums in index order).
+    A tooth that rounding places at or beyond S goes to the last walker whose
+    weight is above 0 (never to a dead walker)."""
     w = np.asarray(weights, dtype=np.float64)
     W = len(w)
     C = np.cumsum(w)                     # running sums, sequential in index order
     step = C[-1] / W
+    last = int(np.nonzero(w > 0)[0][-1])
     n = np.zeros(W, dtype=np.int64)
     i = 0
     for k in range(W):
         t = (k + xi) * step
-        while i < W - 1 and t >= C[i]:
+        while i < last and t >= C[i]:
             i += 1
         n[i] += 1
     return n
@@ -60,7 +63,7 @@ def comb_pairs(n):
 
 def scaled_weights(states):
     """(w_i = exp(ln|w_i| - ref), ref) over alive walkers; dead walkers weigh 0."""
-    lw = np.array([s.logw.real if s.alive else -np.inf for s in states])
+    lw = np.array([s.logw.real if s.alive and math.isfinite(s.logw.real) else -np.inf for s in states])
     ref = np.max(lw)
     return np.where(np.isfinite(lw), np.exp(lw - ref), 0.0), ref
 

@@ -138,3 +138,27 @@ def test_pair_branch_is_unbiased_over_the_draws():
             carried[src] += 2 * nw                                   # two copies of src's state
         acc += carried
     assert np.max(np.abs(acc / grid - w)) < 2e-3 * w.max()
+
+
+def test_leftover_tooth_never_revives_a_dead_walker():
+    """With xi just below 1 the last tooth (W - 1 + xi) S / W rounds to S
+    itself; it belongs to the last walker that carries weight, never to a
+    dead walker in the last slot (a dead walker has weight 0 and, by the
+    comb's definition, an empty interval)."""
+    xi = np.nextafter(1.0, 0.0)
+    rng = np.random.default_rng(0)
+    cases = 0
+    for _ in range(200):
+        W = int(rng.integers(2, 50))
+        w = rng.exponential(size=W)
+        w[-1] = 0.0
+        if W > 3:
+            w[-2] = 0.0
+        C = np.cumsum(w)
+        if (W - 1 + xi) * (C[-1] / W) < C[-1]:
+            continue
+        cases += 1
+        n = comb_counts(w, xi)
+        assert n.sum() == W
+        assert np.all(n[w == 0] == 0)
+    assert cases > 20
