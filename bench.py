@@ -465,6 +465,7 @@ def accuracy_vs_fp64(ftq, torch, dev, W=32):
     c = dict(WORKLOADS[WORKLOAD])
     stream = torch.cuda.current_stream(dev)
     res = {}
+    n = 0
     for name, prec in (("fp64", ftq.FTQ_FP64), ("mixed", ftq.FTQ_MIXED)):
         prop = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, stabilise_every=5,
                               exp_order=6, precision=prec, stream=stream)
@@ -483,7 +484,7 @@ def accuracy_vs_fp64(ftq, torch, dev, W=32):
             "E_per_electron_fp64": res["fp64"]["E_per_electron"], "E_per_electron_mixed": res["mixed"]["E_per_electron"],
             "N_fp64": res["fp64"]["N"], "N_mixed": res["mixed"]["N"],
             "same_killed_walkers": res["fp64"]["alive_mask"] == res["mixed"]["alive_mask"],
-            "walkers": W, "slices": 348, "fields": "seeded N(0,1), identical for both paths"}
+            "walkers": W, "slices": n, "fields": "seeded N(0,1), identical for both paths"}
 
 
 def run_ours(args, rank, world, local_rank):

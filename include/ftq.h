@@ -74,7 +74,8 @@ typedef struct {
     int      overlap;          /* FTQ_OVERLAP_PAPER or FTQ_OVERLAP_MODIFIED               */
     uint64_t seed;             /* key of the on-device field generator (ftq_fields)       */
     void*    cuda_stream;      /* cudaStream_t the library launches on (NULL = default)  */
-    double   force_bias_cap;   /* 0 = off (no cap is applied in this version)             */
+    double   force_bias_cap;   /* must be 0 (no cap: the paper applies none); any other
+                                  value is rejected with FTQ_EINVAL                       */
     double   low_rank_threshold; /* 0 = full rank.  > 0: low-rank truncation (Sec.
                                     "Exploiting the low-rank structure", Eq. thresh) with
                                     this absolute threshold (the paper uses 1e-6): every
@@ -241,6 +242,18 @@ int ftq_ranks(ftq_ctx* ctx, int* ranks_host);
  * unwritten); synchronises the stream. */
 int ftq_status(ftq_ctx* ctx, int* status_host);
 
+/* Test hook of the failure detection (no counterpart in the paper): every
+ * mbarrier wait of the tensor-core chain kernel (mixed precision) polls at
+ * most `polls` times before it gives up; -1 restores the default of 2^24
+ * polls.  A wait that gives up latches FTQ_ETIMEOUT (read by ftq_status), the
+ * kernel skips its remaining work, drains its own copies and MMAs with the
+ * default bound and frees its tensor memory, so the context stays usable: the
+ * chain of that launch is not updated, and ftq_reset starts a clean path.
+ * For a batch context the value applies to the batched launches.  Setting a
+ * small value makes propagation fail; it exists to exercise the timeout path.
+ * Errors: FTQ_EINVAL (NULL context or polls < -1). */
+int ftq_set_wait_limit(ftq_ctx* ctx, int64_t polls);
+
 /* Integer properties. */
 #define FTQ_Q_M          0
 #define FTQ_Q_N_ALPHA    1
@@ -341,7 +354,10 @@ int ftq_profile_read(ftq_ctx* ctx, double* ms_host, int64_t* launches_host);
  * and nothing in the array needs to start at zero.  All calls share the one
  * array: calls that can overlap on the GPU (different streams, or different
  * host threads on the same device) race and must be serialised by the
- * caller.  Asynchronous on cuda_stream; errors via ftq_last_error(NULL). */
+ * caller.  Each call copies the tables from pageable host memory, so it
+ * waits on the host until earlier work on cuda_stream is done before the
+ * copy starts; the kernel then runs asynchronously on cuda_stream.  Errors
+ * via ftq_last_error(NULL). */
 int ftq_estimators_noalloc(int N, int M, double rs, const void* G_dev, int W,
                            double* per_walker_dev, void* cuda_stream);
 

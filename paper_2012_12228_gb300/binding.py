@@ -40,7 +40,7 @@ EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
            "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control", "ftq_structure_factor", "ftq_pair_branch",
-           "ftq_ranks", "ftq_last_error", "ftq_destroy"]
+           "ftq_ranks", "ftq_set_wait_limit", "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
            "border": 7, "fields": 8, "population": 9}
 K_COUNT = 10
@@ -69,6 +69,7 @@ def load_library(path=None):
     lib.ftq_weights.argtypes = [vp, vp]
     lib.ftq_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ftq_ranks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.ftq_set_wait_limit.argtypes = [vp, ctypes.c_int64]
     lib.ftq_query.argtypes = [vp, i, i64p]
     lib.ftq_query_f64.argtypes = [vp, i, dp]
     lib.ftq_basis.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
@@ -323,6 +324,10 @@ class Propagator:
         if pw is not None:
             res["per_walker"] = pw
         return res
+
+    def set_wait_limit(self, polls):
+        """Test hook: polls per mbarrier wait of the tensor-core chain (-1: default)."""
+        self._check(self.lib.ftq_set_wait_limit(self.h, int(polls)), "ftq_set_wait_limit")
 
     def status(self):
         v = ctypes.c_int()

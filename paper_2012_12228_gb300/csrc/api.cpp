@@ -71,6 +71,8 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         return fail(nullptr, FTQ_EINVAL, "unknown constraint");
     if (opts->overlap != FTQ_OVERLAP_PAPER && opts->overlap != FTQ_OVERLAP_MODIFIED)
         return fail(nullptr, FTQ_EINVAL, "unknown overlap");
+    if (opts->force_bias_cap != 0.0)
+        return fail(nullptr, FTQ_EINVAL, "force_bias_cap must be 0: no force-bias cap is implemented");
     if (!(opts->low_rank_threshold >= 0.0) || !std::isfinite(opts->low_rank_threshold))
         return fail(nullptr, FTQ_EINVAL, "low_rank_threshold must be finite and >= 0");
     if (opts->low_rank_threshold > 0.0 && opts->precision != FTQ_FP64)
@@ -342,6 +344,13 @@ int ftq_status(ftq_ctx* c, int* status_host) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "status");
     *status_host = (v & 2) ? FTQ_ETIMEOUT : (v ? FTQ_ENUMERIC : FTQ_OK);
+    return FTQ_OK;
+}
+
+int ftq_set_wait_limit(ftq_ctx* c, int64_t polls) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (polls < -1) return fail(c, FTQ_EINVAL, "polls must be >= -1");
+    c->wait_limit = polls;
     return FTQ_OK;
 }
 

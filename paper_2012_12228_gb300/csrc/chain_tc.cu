@@ -170,6 +170,7 @@ struct TcBatch {
     int qsize_max;
     int m_max;
     int ncols;          // TMEM columns allocated once per CTA
+    long long wait_limit;   // polls per bounded mbarrier wait of the pipeline
 };
 
 // Persistent, warp-specialised kernel over a work list of items (system,
@@ -202,9 +203,10 @@ __device__ __forceinline__ void gen_barrier() {
 
 // Bounded wait that also gives up once another warp has latched an abort;
 // the result is uniform over the calling warp's active lanes.
-__device__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+__device__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                             long long limit) {
     bool ok = false;
-    for (long i = 0; i < WAIT_LIMIT && !ok; ++i) {
+    for (long long i = 0; i < limit && !ok; ++i) {
         if (*abort_flag) break;
         ok = mbar_try_wait(bar, parity);
     }
@@ -279,11 +281,11 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                 const int tb_i = li & 1;
                 const uint32_t acc = tmem + (uint32_t)(tb_i * tb.ncols);
                 // the epilogue of item li - 2 must have released this buffer
-                if (li >= 2) ok = mbar_wait_ab(&tempty[tb_i], (uint32_t)(((li - 2) >> 1) & 1), &abort_sh, st);
+                if (li >= 2) ok = mbar_wait_ab(&tempty[tb_i], (uint32_t)(((li - 2) >> 1) & 1), &abort_sh, st, tb.wait_limit);
                 for (int kt = 0; kt < p.ktiles && ok; ++kt, ++g) {
                     const int s = g & 1, use = g >> 1;
-                    ok = mbar_wait_ab(&afull[s], (uint32_t)(use & 1), &abort_sh, st) &&
-                         mbar_wait_ab(&tma_bar[s], (uint32_t)(use & 1), &abort_sh, st);
+                    ok = mbar_wait_ab(&afull[s], (uint32_t)(use & 1), &abort_sh, st, tb.wait_limit) &&
+                         mbar_wait_ab(&tma_bar[s], (uint32_t)(use & 1), &abort_sh, st, tb.wait_limit);
                     if (!ok) break;
                     tc_fence_after();
                     unsigned char* Ahi = base + s * stage_bytes;
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                     if (kt + 1 == p.ktiles) mma_commit(&tfull[tb_i]);   // accumulator complete
                     last_mma = g;
                     // MMA(g - 1) frees stage s ^ 1 for the next B tile
-                    if (g >= 1) ok = mbar_wait_ab(&mma_bar[s ^ 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st);
+                    if (g >= 1) ok = mbar_wait_ab(&mma_bar[s ^ 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st, tb.wait_limit);
                     if (!ok) break;
                     if (kt + 1 < p.ktiles) issue_tma(it, kt + 1, g + 1);
                     else if (item + (int)gridDim.x < nitems) issue_tma(nx, 0, g + 1);
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
             }
             for (int kt = 0; kt < p.ktiles; ++kt, ++g) {
                 const int s = g & 1, use = g >> 1;
-                if (g >= 2 && !mbar_wait_ab(&mma_bar[s], (uint32_t)((use - 1) & 1), &abort_sh, st)) continue;
+                if (g >= 2 && !mbar_wait_ab(&mma_bar[s], (uint32_t)((use - 1) & 1), &abort_sh, st, tb.wait_limit)) continue;
                 if (abort_sh) continue;
                 unsigned char* Ahi = base + s * stage_bytes;
                 unsigned char* Alo = Ahi + a_bytes;
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
             const int4 it = items[item];
             const TcArgs& p = tb.args[it.x];
             const int tb_i = li & 1;
-            const bool acc_ok = mbar_wait_ab(&tfull[tb_i], (uint32_t)((li >> 1) & 1), &abort_sh, st);
+            const bool acc_ok = mbar_wait_ab(&tfull[tb_i], (uint32_t)((li >> 1) & 1), &abort_sh, st, tb.wait_limit);
             tc_fence_after();
             const int w = it.y, rows0 = it.z * 64, col0 = it.w * p.NT;
             const int r = warp * 32 + lane;               // accumulator row = TMEM lane
@@ -712,6 +714,7 @@ cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double
     tb.m_max = c->M;
     tb.qsize_max = tb.args[0].qsize;
     tb.ncols = tmem_cols(NT);
+    tb.wait_limit = c->wait_limit >= 0 ? (long long)c->wait_limit : (long long)WAIT_LIMIT;
     cudaError_t e = launch_items(c, tb, c->items, c->nitems, c->stream);
     if (e != cudaSuccess) return e;
     return launch_border(c, zin, out, zs, os, alpha);
@@ -736,6 +739,7 @@ cudaError_t tc_chain_step_batch(ftq_ctx* b, const float* const* zin, float* cons
         tb.qsize_max = std::max(tb.qsize_max, tb.args[s].qsize);
         tb.ncols = std::max(tb.ncols, tmem_cols(NT));
     }
+    tb.wait_limit = b->wait_limit >= 0 ? (long long)b->wait_limit : (long long)WAIT_LIMIT;
     cudaError_t e = launch_items(b, tb, b->items, b->nitems, b->stream);
     for (int s = 0; s < ns && e == cudaSuccess; ++s) {
         ftq_ctx* c = b->members[s];

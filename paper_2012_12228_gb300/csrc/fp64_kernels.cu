@@ -424,8 +424,12 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
                 s[8] += dlnS.x;
                 s[11] += dlnS.y;
             } else if (s[2] > 0.5) {
-                double cth = cos(lnS.y);
-                if (cth <= 0.0) {
+                const double cth = cos(lnS.y);
+                if (!isfinite(lnS.x + gr) || !(cth == cth)) {
+                    // a non-finite ratio or Gaussian factor drops the walker (weight 0)
+                    s[2] = 0.0;
+                    atomicOr(status, 1);
+                } else if (cth <= 0.0) {
                     s[2] = 0.0;
                 } else {
                     s[0] += lnS.x + gr + log(cth);
@@ -502,14 +506,17 @@ __global__ void k_reduce_walkers(const double* __restrict__ est, double* __restr
     double best = -INFINITY;
     int bi = W;
     for (int w = threadIdx.x; w < W; w += blockDim.x)
-        if (est[(long)WSTRIDE * w + 2] > 0.5 && est[(long)WSTRIDE * w] > best) { best = est[(long)WSTRIDE * w]; bi = w; }
+        if (est[(long)WSTRIDE * w + 2] > 0.5 && isfinite(est[(long)WSTRIDE * w]) && est[(long)WSTRIDE * w] > best) {
+            best = est[(long)WSTRIDE * w];
+            bi = w;
+        }
     int wm = block_argmax(best, bi, shv, shi);
     double s = wm < W ? est[(long)WSTRIDE * wm] : 0.0;
     double2 sw = make_double2(0.0, 0.0), swe = sw, swn = sw;
     double nal = 0.0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
         const double* o = est + (long)WSTRIDE * w;
-        if (o[2] <= 0.5) continue;
+        if (o[2] <= 0.5 || !isfinite(o[0])) continue;     // a non-finite ln|w| weighs 0
         double m = exp(o[0] - s);
         double2 ww = make_double2(m * cos(o[1]), m * sin(o[1]));
         sw = sw + ww;

@@ -97,6 +97,7 @@ struct ftq_ctx {
     alignas(64) unsigned char tmap[3][128] = {};
     const float* tmap_buf[3] = {nullptr, nullptr, nullptr};
     int nct = 1;                  // column tiles of the tensor-core chain (autotuned)
+    int64_t wait_limit = -1;      // polls per mbarrier wait of the tensor-core chain (-1: default)
     int4* items = nullptr;        // work list of the tensor-core chain
     int nitems = 0;
     // ragged batch: member systems (owned), CUDA graph of the last propagation

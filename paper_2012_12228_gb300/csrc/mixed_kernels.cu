@@ -309,8 +309,12 @@ __global__ void k_green32(const float* __restrict__ Ypl, const double2* __restri
             s[8] += dlnS.x;
             s[11] += dlnS.y;
         } else if (s[2] > 0.5) {
-            double cth = cos(lnS.y);
-            if (cth <= 0.0) {
+            const double cth = cos(lnS.y);
+            if (!isfinite(lnS.x + gr) || !(cth == cth)) {
+                // a non-finite ratio or Gaussian factor drops the walker (weight 0)
+                s[2] = 0.0;
+                atomicOr(status, 1);
+            } else if (cth <= 0.0) {
                 s[2] = 0.0;
             } else {
                 s[0] += lnS.x + gr + log(cth);

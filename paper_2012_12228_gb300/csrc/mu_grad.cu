@@ -162,7 +162,7 @@ __global__ void k_reduce_dmu(const double* __restrict__ est, double* __restrict_
     double best = -INFINITY;
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
         const double* o = est + (long)WSTRIDE * w;
-        if (o[2] > 0.5 && o[0] > best) best = o[0];
+        if (o[2] > 0.5 && isfinite(o[0]) && o[0] > best) best = o[0];
     }
     for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_down_sync(0xffffffffu, best, off));
     if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = best;
@@ -178,7 +178,7 @@ __global__ void k_reduce_dmu(const double* __restrict__ est, double* __restrict_
     int nal = 0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
         const double* o = est + (long)WSTRIDE * w;
-        if (o[2] <= 0.5) continue;
+        if (o[2] <= 0.5 || !isfinite(o[0])) continue;     // a non-finite ln|w| weighs 0
         const double m = exp(o[0] - s);
         const double2 ww = make_double2(m * cos(o[1]), m * sin(o[1]));
         const double2 E = make_double2(o[3], o[4]), Nn = make_double2(o[5], o[6]);

@@ -5,7 +5,7 @@
 // parallel; then one thread forms the running sums C_i in index order in
 // FP64, places the W teeth t_k = (k + xi) (S / W) (S = C_{W-1}), counts the
 // copies n_i (walker i takes the teeth in [C_{i-1}, C_i), the last walker
-// the rest), pairs the extra copies (ascending source) with the walkers that
+// with a weight above 0 the rest), pairs the extra copies (ascending source) with the walkers that
 // got none (ascending slot) and gives every surviving walker the weight S / W
 // (ln|w| = ln(S / W) + max, phase 0).  k_copy_walkers then copies the whole
 // walker state of each source into its destination slot; sources are
@@ -36,7 +36,7 @@ __global__ void k_comb(double* __restrict__ ws, double* __restrict__ wsc_g, int*
     double m = -INFINITY;
     for (int i = tid; i < W; i += nt) {
         const double* s = ws + (long)WSTRIDE * i;
-        if (s[2] > 0.5 && s[0] > m) m = s[0];
+        if (s[2] > 0.5 && isfinite(s[0]) && s[0] > m) m = s[0];
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((tid & 31) == 0) shm[tid >> 5] = m;
@@ -53,19 +53,25 @@ __global__ void k_comb(double* __restrict__ ws, double* __restrict__ wsc_g, int*
     }
     for (int i = tid; i < W; i += nt) {
         const double* s = ws + (long)WSTRIDE * i;
-        wsc[i] = s[2] > 0.5 ? exp(s[0] - ref) : 0.0;
+        wsc[i] = (s[2] > 0.5 && isfinite(s[0])) ? exp(s[0] - ref) : 0.0;   // non-finite ln|w| weighs 0
     }
     __syncthreads();
     if (tid != 0) return;
     double S = 0.0;
-    for (int i = 0; i < W; ++i) S += wsc[i];
+    int last = 0;                              // the last walker with a weight above 0
+    for (int i = 0; i < W; ++i) {
+        S += wsc[i];
+        if (wsc[i] > 0.0) last = i;
+    }
     const double step = S / (double)W;
     int k = 0;
     double C = 0.0;
     for (int i = 0; i < W; ++i) {
         C += wsc[i];
         int n = 0;
-        while (k < W && (i == W - 1 || ((double)k + xi) * step < C)) {
+        // teeth that rounding places at or beyond S go to the last walker
+        // that carries weight, never to a dead one
+        while (k < W && i <= last && (i == last || ((double)k + xi) * step < C)) {
             ++n;
             ++k;
         }
@@ -114,7 +120,7 @@ __global__ void k_pair_branch(double* __restrict__ ws, const double* __restrict_
     double m = -INFINITY;
     for (int i = tid; i < W; i += nt) {
         const double* s = ws + (long)WSTRIDE * i;
-        if (s[2] > 0.5 && s[0] > m) m = s[0];
+        if (s[2] > 0.5 && isfinite(s[0]) && s[0] > m) m = s[0];
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((tid & 31) == 0) shm[tid >> 5] = m;
@@ -132,7 +138,7 @@ __global__ void k_pair_branch(double* __restrict__ ws, const double* __restrict_
     }
     for (int i = tid; i < W; i += nt) {
         const double* s = ws + (long)WSTRIDE * i;
-        wsc[i] = s[2] > 0.5 ? exp(s[0] - ref) : 0.0;
+        wsc[i] = (s[2] > 0.5 && isfinite(s[0])) ? exp(s[0] - ref) : 0.0;   // non-finite ln|w| weighs 0
     }
     __syncthreads();
     if (tid == 0) {

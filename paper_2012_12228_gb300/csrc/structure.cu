@@ -66,7 +66,7 @@ __global__ void k_struct_weights(const double* __restrict__ ws, double2* __restr
     double m = -INFINITY;
     for (int i = tid; i < W; i += nt) {
         const double* s = ws + (long)WSTRIDE * i;
-        if (s[2] > 0.5 && s[0] > m) m = s[0];
+        if (s[2] > 0.5 && isfinite(s[0]) && s[0] > m) m = s[0];
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((tid & 31) == 0) shm[tid >> 5] = m;
@@ -79,7 +79,7 @@ __global__ void k_struct_weights(const double* __restrict__ ws, double2* __restr
     for (int i = tid; i < W; i += nt) {
         const double* s = ws + (long)WSTRIDE * i;
         double2 v = make_double2(0.0, 0.0);
-        if (s[2] > 0.5) {
+        if (s[2] > 0.5 && isfinite(s[0])) {
             const double mag = exp(s[0] - ref);
             v = make_double2(mag * cos(s[1]), mag * sin(s[1]));
             nal += 1.0;

@@ -51,9 +51,14 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ftq_init_ueg(ctypes.byref(h), 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
     assert b"overlap" in lib.ftq_last_error(None)
     o.overlap = 0
+    o.force_bias_cap = 0.5
+    assert lib.ftq_init_ueg(ctypes.byref(h), 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
+    assert b"force_bias_cap" in lib.ftq_last_error(None)
+    o.force_bias_cap = 0.0
     o.walkers = 0
     assert lib.ftq_init_ueg(ctypes.byref(h), 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
     assert lib.ftq_init_ueg(None, 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
+    assert lib.ftq_set_wait_limit(None, 0) == -1
     lib.ftq_destroy(None)
 
 
