@@ -479,6 +479,50 @@ def run(sys: UEG, fields, opts: Options = None, n_slices=None, record=False,
             for w in range(W)]
 
 
+def slice_estimates(sys: UEG, fields, opts: Options = None, every=1, per_walker=False):
+    """Global estimates E(tau_k), N(tau_k) after every `every`-th slice and
+    their average over those slices (Results, "Assessing the Phaseless
+    Constraint": "No Average" is the estimate at tau = beta, "Average" the
+    global estimate averaged over the time slices).
+
+    All walkers advance together; after slice k the estimate is
+    sum_i w_i,k O_L,i,k / sum_i w_i,k with the weights of slice k and the
+    local values from G(tau_k) (reading P), real parts taken as in reading L
+    (complex weights in free projection).  Reading (the paper gives no
+    formula): every recorded slice counts once in the average.
+    Returns (ks, E_k, N_k, E_avg, N_avg) with complex E_k, N_k; with
+    per_walker=True also a list over the recorded slices of (w, E_L, N_L)
+    arrays (the scaled weights and local values of every walker)."""
+    opts = opts or Options()
+    n, W = fields.shape[0], fields.shape[1]
+    states = [initial_state(sys) for _ in range(W)]
+    ks, Es, Ns, rows = [], [], [], []
+    for k in range(1, n + 1):
+        states = [slice_step(sys, st, fields[k - 1, w], k, opts)[0] for w, st in enumerate(states)]
+        if k % every:
+            continue
+        res = [WalkerResult(st.logw, st.alive, st.G, st.logdet, *local_energy(sys, st.G)) for st in states]
+        if opts.constraint == "free":
+            lw = np.array([r.logw for r in res])
+            w = np.exp(lw - np.max(lw.real))
+        else:
+            ok = np.array([r.alive and math.isfinite(r.logw.real) for r in res])
+            lw = np.where(ok, np.array([r.logw.real for r in res]), -np.inf)
+            w = np.where(ok, np.exp(lw - np.max(lw)), 0.0)
+        EL = np.array([r.energy for r in res])
+        NL = np.array([r.number for r in res])
+        E = np.sum(w * EL) / np.sum(w)
+        Nn = np.sum(w * NL) / np.sum(w)
+        if per_walker:
+            rows.append((w, EL, NL))
+        ks.append(k)
+        Es.append(E)
+        Ns.append(Nn)
+    Es, Ns = np.array(Es), np.array(Ns)
+    out = (ks, Es, Ns, float(np.mean(Es.real)), float(np.mean(Ns.real)))
+    return out + (rows,) if per_walker else out
+
+
 def weighted_estimate(results, constraint="phaseless"):
     """<O> = sum_i w_i O_i / sum_i w_i (Theory: importance-sampled estimator).
 

@@ -227,3 +227,47 @@ def gaussian_state_average(M, X, ops):
         for n, O in enumerate(ops):
             traces[n] += np.sum(U * O[idx][:, idx].toarray().T)
     return traces / Z, np.log(Z)
+
+
+def mixed_estimate(sys: UEG, a, b, mu=None, interacting=True):
+    """Exact <O> = tr(e^{-a (H - mu N)} e^{-b H_T} O) / tr(e^{-a (H - mu N)} e^{-b H_T})
+    for O = H (including E_M) and O = N, with the free-electron trial
+    H_T = sum_{k,s} (|K|^2/2 - mu_T) n_{k,s} (Eq. Abrenda with the FE trial of
+    Computational Details).  This is what the estimator at tau_k = k dtau
+    approaches without a constraint: the walkers' propagators average to
+    e^{-k dtau (H - mu N)} and the trial block B_T^(n-k) follows them
+    (reading P), so a = k dtau and b = (n - k) dtau.  Returns complex values
+    (the two factors do not commute)."""
+    mu = sys.mu if mu is None else mu
+    H, n_up, n_dn, ktot = hamiltonian(sys, interacting)
+    dim = H.shape[0]
+    states = np.arange(dim, dtype=np.int64)
+    ht = np.zeros(dim)
+    for s in range(2):
+        for k in range(sys.M):
+            ht += (sys.eps[k] - sys.mu_T) * ((states >> (s * sys.M + k)) & 1)
+    nn = (n_up + n_dn).astype(np.float64)
+    keys = np.concatenate([n_up[:, None], n_dn[:, None], ktot], axis=1)
+    _, inverse = np.unique(keys, axis=0, return_inverse=True)
+    inverse = inverse.reshape(-1)
+    order = np.argsort(inverse, kind="stable")
+    bounds = np.flatnonzero(np.diff(inverse[order])) + 1
+    blocks = []
+    shift = None
+    for idx in np.split(order, bounds):
+        h = H[idx][:, idx].toarray()
+        ev, V = np.linalg.eigh(0.5 * (h + h.conj().T))
+        x = -a * (ev - mu * nn[idx[0]])
+        y = -b * ht[idx]
+        m = x.max() + y.max()
+        shift = m if shift is None else max(shift, m)
+        blocks.append((idx, h, ev, V, x, y))
+    Z = E = Nn = 0j
+    for idx, h, ev, V, x, y in blocks:
+        # e^{-a (H - mu N)} e^{-b H_T} on this block, scaled by e^{-shift}
+        U = (V * np.exp(x - 0.5 * shift)[None, :]) @ V.conj().T
+        U = U * np.exp(y - 0.5 * shift)[None, :]
+        Z += np.trace(U)
+        E += np.sum(U * h.T)
+        Nn += np.trace(U) * nn[idx[0]]
+    return E / Z + sys.E_M, Nn / Z
