@@ -35,9 +35,13 @@ from synthetic_inputs import RAGGED, WORKLOADS, gaussian_fields  # noqa: E402
 METRIC = "walker-slices/sec at M=257 (mixed vs FP64, same GB300) at ≤1e-5 Ha/e error"
 WORKLOAD = "ueg_n66_m257"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 FMA pipe: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal
-# 1.25 TFLOP/s for this part); a register-loop FMA probe measured 1.20.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Pipe peaks from the SM count (device properties), the maximum SM clock
+# (MEASURED_PEAKS.json, driver-written) and the per-SM issue rates of this
+# part: 2 FP64 FMA and 128 FP32 FMA per clock per SM, 2 flop per FMA
+# (nominal FP64 1.25 TFLOP/s).  Set by set_device_peaks() once the device is
+# known; the defaults below are the same formula for 152 SMs at 2.07 GHz.
+SMS, SM_GHZ = 152, 2.07
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_GHZ * 1e9 / 1e12
 
 
 def parse():
@@ -51,6 +55,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed-vs-FP64 energy check")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged-batch measurement")
+    ap.add_argument("--no-configs", action="store_true", help="skip the M=57 and M=123 whole-path lines")
     ap.add_argument("--walkers", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lowrank", action="store_true",
@@ -158,8 +163,17 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline
 PEAKS = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-# FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_GHZ * 1e9 / 1e12
+
+
+def set_device_peaks(torch, dev):
+    """SM count from the device properties and the maximum SM clock from
+    MEASURED_PEAKS.json (else 2.07 GHz); recomputes the pipe peaks."""
+    global SMS, SM_GHZ, FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS
+    SMS = torch.cuda.get_device_properties(dev).multi_processor_count
+    SM_GHZ = PEAKS.get("sm_max_mhz", 2070.0) / 1e3
+    FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_GHZ * 1e9 / 1e12
+    FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_GHZ * 1e9 / 1e12
 
 # DRAM bytes (read + write) per walker and launch from one ncu capture of the
 # kernel as it stands (files under profiles/); the launches process walkers
@@ -168,7 +182,6 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TRAFFIC_PER_WALKER = {
     ("mixed", "green"): (1.054e9 / 128, "profiles/green32b_ueg_n66_m257_w128.md"),
     ("mixed", "chain"): (0.3198e9 / 128, "profiles/chain_tc_ueg_n66_m257_w128.md"),
-    ("mixed", "qrcp"): (20.199e9 / 128, "profiles/qr_prepiv64_ueg_n66_m257_w128.md"),
     ("fp64", "chain"): (0.3867e9 / 128, "profiles/chain_fp64_ueg_n66_m257_w128.md"),
 }
 
@@ -180,8 +193,10 @@ def kernel_model(kind, M, W, precision):
     the complex product as three tf32 products (3xTF32), so its tensor work is
     3 x 8 M^3 per walker and its peak is the tf32 dense rate: the measured
     bf16 GEMM rate times the nominal tf32/bf16 ratio 1.1/2.25."""
-    fp64 = ("alu", FP64_PEAK_TFLOPS, "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz")
-    fp32 = ("alu", FP32_PEAK_TFLOPS, "FP32 FMA pipe: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz")
+    fp64 = ("alu", FP64_PEAK_TFLOPS, f"FP64 FMA pipe: {SMS} SMs (device properties) x 2 DFMA/clk x 2 x "
+                                      f"{SM_GHZ:.2f} GHz (max SM clock)")
+    fp32 = ("alu", FP32_PEAK_TFLOPS, f"FP32 FMA pipe: {SMS} SMs (device properties) x 128 FMA/clk x 2 x "
+                                      f"{SM_GHZ:.2f} GHz (max SM clock)")
     bf16 = PEAKS.get("bf16_tflops", 1900.0)
     tf32 = ("tensor", bf16 * 1.1 / 2.25,
             f"tf32 dense = measured bf16 {bf16:.1f} TFLOP/s x 1.1/2.25 (MEASURED_PEAKS.json)"
@@ -195,7 +210,9 @@ def kernel_model(kind, M, W, precision):
     if kind == "qrcp":
         if precision == "fp64":  # Householder QR (16/3) + forming Q (16/3) + T^-1 update (4)
             return ((16.0 / 3.0 + 16.0 / 3.0 + 4.0) * M ** 3 * W,) + fp64
-        return ((16.0 / 3.0 + 4.0) * M ** 3 * W,) + fp64     # Q is formed in FP32 (bridge class)
+        return ((16.0 / 3.0) * M ** 3 * W,) + fp32          # FP32 Householder of Y Pi (Q: bridge class)
+    if kind == "tinv":           # T^-1 <- T^-1 Pi U^-1: a triangular solve with M right-hand sides
+        return (4.0 * M ** 3 * W,) + fp64
     return None
 
 
@@ -311,9 +328,43 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     out["kernel_ms_per_step"] = {k: v["ms"] for k, v in prof.items() if v["ms"] > 0}
     out["roofline"] = roofline(prof, M, W, precision)
     out["device_status"] = prop.status()
+    out["slice_average"] = measure_tracking(torch, prop, stream, fields)
     out["population_control"] = measure_comb(torch, prop, stream, precision, fields)
     prop.close()
     return out
+
+
+def measure_tracking(torch, prop, stream, fields):
+    """Cost of the time-slice estimates (Results, the slice-averaged
+    estimator): one block of 5 slices with the estimators evaluated and
+    recorded after every slice, against the same block without; and one
+    estimator evaluation at tau_k alone (CUDA events on the launching
+    stream)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for every in (0, 1):
+        prop.reset()
+        prop.propagate(fields[0])
+        prop.track_estimates(every)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        prop.propagate(fields[1])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[every] = e0.elapsed_time(e1)
+    prop.track_estimates(0)
+    before = prop.profile_read()
+    prop.profile(True)
+    prop.estimators(per_walker=False)
+    after = prop.profile_read()
+    prop.profile(False)
+    est_ms = after["estimators"][0] - 0.0
+    prop.reset()
+    return {"ms_per_block_plain": res[0], "ms_per_block_tracked": res[1],
+            "overhead_ms_per_slice": (res[1] - res[0]) / 5.0,
+            "estimator_ms_per_call_c128": est_ms,
+            "note": "5-slice block with the estimators of every slice recorded vs without; "
+                    "estimator call on the complex128 G at tau_k"}
 
 
 def measure_comb(torch, prop, stream, precision, fields):
@@ -374,8 +425,78 @@ def measure_ragged(ftq, torch, dev, steps=4, warmup=3):
            "warmup": warmup, "gpu_launches": b.launches() - l0, "graph": "one CUDA graph launch per step",
            "systems": [dict(N=sd["N"], M=sd["M"], rs=sd["rs"], theta=sd["theta"], dtau=sd["dtau"],
                             walkers=sd["walkers"], column_tiles=t[0]) for sd, t in zip(RAGGED, tuned)]}
+    # per-kernel times of one block (event timing turns the graph off for this block)
+    ctxs = [b] + b.members
+    for c in ctxs:
+        c.profile(True)
+    res["roofline"] = ragged_roofline(b, fl, stab, ctxs)
+    for c in ctxs:
+        c.profile(False)
     b.close()
+    res["sequential"] = measure_ragged_sequential(ftq, torch, dev, steps, warmup)
+    res["batch_over_sequential"] = res["value"] / res["sequential"]["value"]
     return res
+
+
+def ragged_roofline(b, fl, stab, ctxs):
+    """Dominant kernel class of one batched block of 5 slices (the members
+    are reset and run their first block again) with its algorithmic flops
+    summed over the systems."""
+    for m in b.members:
+        m.reset()
+    b.propagate([f[0:stab].contiguous() for f in fl])
+    prof = [c.profile_read() for c in ctxs]
+    kinds = {}
+    for p in prof:
+        for k, (ms, _) in p.items():
+            kinds[k] = kinds.get(k, 0.0) + ms
+    dom = max(kinds, key=lambda k: kinds[k])
+    flops = 0.0
+    model = None
+    for sd, m in zip(RAGGED, b.members):
+        per_block = {"chain": 6 * stab, "green": stab, "qrcp": 1, "tinv": 1}.get(dom, 0)
+        mm = kernel_model(dom, m.M, m.W, "mixed")
+        if mm is None or per_block == 0:
+            model = None
+            break
+        model = mm
+        flops += mm[0] * per_block
+    out = {"kernel": dom, "ms_per_block_by_kernel": kinds}
+    if model is not None:
+        ach = flops / (kinds[dom] / 1e3) / 1e12
+        out.update({"bound": model[1], "achieved": ach, "peak": model[2], "unit": "TFLOP/s",
+                    "frac": ach / model[2], "peak_source": model[3]})
+    return out
+
+
+def measure_ragged_sequential(ftq, torch, dev, steps, warmup):
+    """The same four systems run one after another as separate contexts
+    (mixed precision, autotuned column tiles, same fields and block count):
+    the sum of their times is what the batch replaces."""
+    stab = 5
+    total_ms = 0.0
+    ws = 0
+    stream = torch.cuda.current_stream(dev)
+    for sd in RAGGED:
+        p = ftq.Propagator(sd["N"], sd["M"], sd["rs"], sd["theta"], sd["dtau"], walkers=sd["walkers"],
+                           precision=ftq.FTQ_MIXED, stream=stream)
+        p.autotune()
+        f = torch.from_numpy(gaussian_fields(sd["seed"], (warmup + steps) * stab, sd["walkers"],
+                                             p.n_alpha)).to(dev)
+        for s_ in range(warmup):
+            p.propagate(f[s_ * stab:(s_ + 1) * stab].contiguous())
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s_ in range(warmup, warmup + steps):
+            p.propagate(f[s_ * stab:(s_ + 1) * stab].contiguous())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += e0.elapsed_time(e1)
+        ws += sd["walkers"] * stab * steps
+        p.close()
+    return {"value": ws / (total_ms / 1e3), "unit": "walker-slices/s", "ms_per_step": total_ms / steps,
+            "note": "the four systems as four contexts, one after another, same steps"}
 
 
 LOWRANK = dict(N=14, M=515, rs=0.5, theta=0.125, dtau=0.05, seed=1240)
@@ -459,6 +580,46 @@ def compression_trace(ftq, torch, dev, stream, theta, thr, W=16, dtau=0.01):
             "mean_compression_T": float(np.mean([1.0 - r["m_T"] / M for r in rows]))}
 
 
+def measure_config(ftq, torch, dev, wl, precision, with_mu=False):
+    """Walker-slices/s of the whole path (all n slices, the estimators at
+    tau = beta) of a smaller workload at its own walker count; with_mu adds
+    the chemical-potential derivative (forward accumulation along the path,
+    evaluated by ftq_mu_grad at tau = beta) and its cost."""
+    c = dict(WORKLOADS[wl])
+    W = c["walkers"]
+    stream = torch.cuda.current_stream(dev)
+    prec = ftq.FTQ_FP64 if precision == "fp64" else ftq.FTQ_MIXED
+    p = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, precision=prec, stream=stream)
+    if precision == "mixed":
+        p.autotune()
+    n = p.n_slices
+    f = torch.from_numpy(gaussian_fields(c["seed"], n, W, p.n_alpha)).to(dev)
+    p.propagate(f[:5].contiguous())            # warm-up
+    p.reset()
+    torch.cuda.synchronize(dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    l0 = p.launches()
+    e0.record(stream)
+    p.propagate(f)
+    est = p.estimators(per_walker=False)
+    e1.record(stream)
+    out = {"workload": wl, "precision": precision, "N": c["N"], "M": p.M, "walkers": W, "n_slices": n}
+    if with_mu:
+        g = p.mu_grad(per_walker=False)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        out["mu_derivative"] = {"dN_dmu": g["dN"], "dE_dmu": g["dE"], "ms_mu_grad_call": e1.elapsed_time(e2),
+                                "note": "tangents accumulated in the Green epilogues of every slice; "
+                                        "ftq_mu_grad evaluates them at tau = beta"}
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    out.update({"value": W * n / (ms / 1e3), "unit": "walker-slices/s", "ms_path": ms,
+                "gpu_launches": int(p.launches() - l0), "E_per_electron": est["E"].real / c["N"],
+                "N": est["N"].real, "alive": est["n_alive"], "status": p.status()})
+    p.close()
+    return out
+
+
 def accuracy_vs_fp64(ftq, torch, dev, W=32):
     """E/N at tau = beta of the mixed and the complex128 path on identical
     fields (whole path, W walkers)."""
@@ -495,6 +656,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    set_device_peaks(torch, dev)
     c = dict(WORKLOADS[WORKLOAD])
     W = args.walkers or c["walkers"]
 
@@ -521,6 +683,10 @@ def run_ours(args, rank, world, local_rank):
     ragged = None
     if args.precision == "mixed" and not args.no_ragged and rank == 0:
         ragged = measure_ragged(ftq, torch, dev)
+    others = None
+    if args.precision == "mixed" and not args.no_configs and rank == 0:
+        others = {"ueg_n14_m57": {p_: measure_config(ftq, torch, dev, "ueg_n14_m57", p_) for p_ in ("mixed", "fp64")},
+                  "ueg_n14_m123": measure_config(ftq, torch, dev, "ueg_n14_m123", "fp64", with_mu=True)}
     if rank != 0:
         return
     line = {
@@ -544,6 +710,7 @@ def run_ours(args, rank, world, local_rank):
         "estimate": head["estimate"],
         "device_status": head["device_status"],
         "population_control": head["population_control"],
+        "slice_average": head["slice_average"],
     }
     if comparison:
         line["fp64_path"] = {"value": comparison["value"], "ms_per_step": comparison["ms_per_step"],
@@ -555,6 +722,8 @@ def run_ours(args, rank, world, local_rank):
         line["error_vs_fp64"] = acc
     if ragged:
         line["ragged_batch"] = ragged
+    if others:
+        line["other_configs"] = others
     if lowrank:
         line["low_rank"] = lowrank
     if head.get("autotune"):

@@ -254,6 +254,31 @@ int ftq_status(ftq_ctx* ctx, int* status_host);
  * Errors: FTQ_EINVAL (NULL context or polls < -1). */
 int ftq_set_wait_limit(ftq_ctx* ctx, int64_t polls);
 
+/* Time-slice estimates and their average (Results, "Assessing the Phaseless
+ * Constraint": "No Average" is the global estimate at tau = beta, "Average"
+ * the global estimate averaged over the time slices).  After
+ * ftq_track_estimates(ctx, every) with every > 0, each slice k propagated by
+ * ftq_propagate_slices with k % every == 0 is followed by the estimators of
+ * every walker from G(tau_k) (the complex128 path: complex128 G; the mixed
+ * path: the FP32 G of the slice, complex128 at tau = beta) and by the
+ * weighted global estimate of slice k, E_k = sum_w w_k E_L / sum_w w_k and
+ * N_k likewise (w_k the walkers' weights at slice k, complex in free
+ * projection), recorded on the device.  every = 0 stops recording;
+ * ftq_reset clears the record.  Not for batch contexts.
+ * Errors: FTQ_EINVAL (every < 0, a batch context), FTQ_ENOMEM. */
+int ftq_track_estimates(ftq_ctx* ctx, int every);
+
+/* Read the recorded slice estimates; synchronises the stream.
+ *   out_host  host float64 [1 + capacity][8].  Row 0: {n recorded, Re E_avg,
+ *             Im E_avg, Re N_avg, Im N_avg, 0, 0, 0}, the averages over the
+ *             recorded slices of E_k and N_k (each slice counts once).  Row r
+ *             (1 <= r <= min(n, capacity)): {k, Re E_k, Im E_k, Re N_k, Im N_k,
+ *             alive walkers, Re of the sum of the scaled weights, ln of the
+ *             scale} for the r-th recorded slice.
+ * Errors: FTQ_EINVAL (NULL buffer, capacity < 0, tracking never enabled),
+ * FTQ_ECUDA. */
+int ftq_slice_estimates(ftq_ctx* ctx, double* out_host, int capacity);
+
 /* Integer properties. */
 #define FTQ_Q_M          0
 #define FTQ_Q_N_ALPHA    1
@@ -289,7 +314,10 @@ int ftq_transfers(const ftq_ctx* ctx, int32_t* q_host);
  * opts->cuda_stream on entry and before it on exit of every call.  The
  * member systems are ordinary contexts (ftq_batch_member) for ftq_green,
  * ftq_estimators, ftq_weights and ftq_mu_grad; they are destroyed with the
- * batch.  Not a construct of the paper: it batches independent instances of
+ * batch.  A member keeps running on the batch's stream: every call on it that
+ * reads or writes caller device memory first waits for opts->cuda_stream and
+ * then makes opts->cuda_stream wait for its own work, so buffers of the
+ * caller's stream are safe to use around it.  Not a construct of the paper: it batches independent instances of
  * its slice path (Sec. Computational Details: many independent simulations). */
 int ftq_init_batch(ftq_ctx** out, int nsys, const ftq_system* systems, const ftq_opts* opts);
 int ftq_batch_member(ftq_ctx* batch, int index, ftq_ctx** member);
@@ -308,7 +336,7 @@ int ftq_autotune(ftq_ctx* ctx, int* choice, float* ms);
 /* Kernel classes for launch accounting and timing. */
 #define FTQ_K_FORCE_BIAS 0   /* force bias + shifted fields + V generator table   */
 #define FTQ_K_CHAIN      1   /* one Taylor-Horner step of exp(V) on the chain       */
-#define FTQ_K_QRCP       2   /* QRCP stabilisation of the right block              */
+#define FTQ_K_QRCP       2   /* QRCP stabilisation (mixed: pre-pivoted FP32 QR)      */
 #define FTQ_K_GREEN      3   /* G(tau), ln det(I + A) and the weight update         */
 #define FTQ_K_ESTIMATORS 4   /* per-walker estimators and the walker reduction      */
 #define FTQ_K_INIT       5   /* walker initialisation / reset                      */
@@ -316,7 +344,8 @@ int ftq_autotune(ftq_ctx* ctx, int* choice, float* ms);
 #define FTQ_K_BORDER     7   /* chain entries outside the tensor-core tile         */
 #define FTQ_K_FIELDS     8   /* on-device auxiliary-field generator                */
 #define FTQ_K_POPULATION 9   /* comb population control                            */
-#define FTQ_K_COUNT      10
+#define FTQ_K_TINV       10  /* mixed path: FP64 update of D_R and T^-1 after the QR */
+#define FTQ_K_COUNT      11
 
 /* Start (enable != 0) or stop per-launch timing.  While on, every kernel
  * launch is bracketed by a CUDA event pair on the context's stream; enabling

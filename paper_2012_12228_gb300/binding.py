@@ -40,10 +40,11 @@ EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
            "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control", "ftq_structure_factor", "ftq_pair_branch",
-           "ftq_ranks", "ftq_set_wait_limit", "ftq_last_error", "ftq_destroy"]
+           "ftq_ranks", "ftq_set_wait_limit", "ftq_track_estimates", "ftq_slice_estimates",
+           "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
-           "border": 7, "fields": 8, "population": 9}
-K_COUNT = 10
+           "border": 7, "fields": 8, "population": 9, "tinv": 10}
+K_COUNT = 11
 
 
 def library_path():
@@ -70,6 +71,8 @@ def load_library(path=None):
     lib.ftq_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ftq_ranks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ftq_set_wait_limit.argtypes = [vp, ctypes.c_int64]
+    lib.ftq_track_estimates.argtypes = [vp, i]
+    lib.ftq_slice_estimates.argtypes = [vp, dp, i]
     lib.ftq_query.argtypes = [vp, i, i64p]
     lib.ftq_query_f64.argtypes = [vp, i, dp]
     lib.ftq_basis.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
@@ -325,6 +328,24 @@ class Propagator:
             res["per_walker"] = pw
         return res
 
+    def track_estimates(self, every=1):
+        """Record the global estimate after every `every`-th slice (0 stops)."""
+        self._check(self.lib.ftq_track_estimates(self.h, int(every)), "ftq_track_estimates")
+
+    def slice_estimates(self):
+        """The recorded slice estimates: dict(k, E, N (complex arrays), alive,
+        E_avg, N_avg (complex): the averages over the recorded slices)."""
+        import numpy as np
+        cap = self.n_slices
+        buf = (ctypes.c_double * (8 * (cap + 1)))()
+        self._check(self.lib.ftq_slice_estimates(self.h, buf, cap), "ftq_slice_estimates")
+        a = np.frombuffer(buf, dtype=np.float64).reshape(cap + 1, 8)
+        n = int(a[0, 0])
+        r = a[1:1 + n]
+        return {"k": r[:, 0].astype(int), "E": r[:, 1] + 1j * r[:, 2], "N": r[:, 3] + 1j * r[:, 4],
+                "alive": r[:, 5].astype(int), "E_avg": complex(a[0, 1], a[0, 2]),
+                "N_avg": complex(a[0, 3], a[0, 4])}
+
     def set_wait_limit(self, polls):
         """Test hook: polls per mbarrier wait of the tensor-core chain (-1: default)."""
         self._check(self.lib.ftq_set_wait_limit(self.h, int(polls)), "ftq_set_wait_limit")
@@ -441,6 +462,20 @@ class Batch:
         if st != 0:
             raise FTQError(f"ftq_autotune: {self.lib.ftq_last_error(self.h).decode()} (status {st})")
         return [(ch[k], ms[k]) for k in range(n)]
+
+    def profile(self, enable=True):
+        """Per-launch event timing of the batched launches (the graph is not
+        used while a member is profiled)."""
+        if self.lib.ftq_profile(self.h, 1 if enable else 0) != 0:
+            raise FTQError("ftq_profile failed")
+
+    def profile_read(self):
+        """{kernel: (summed event ms, launches)} of the batched launches."""
+        ms = (ctypes.c_double * K_COUNT)()
+        n = (ctypes.c_int64 * K_COUNT)()
+        if self.lib.ftq_profile_read(self.h, ms, n) != 0:
+            raise FTQError("ftq_profile_read failed")
+        return {k: (ms[v], n[v]) for k, v in KERNELS.items()}
 
     def launches(self):
         ms = (ctypes.c_double * K_COUNT)()

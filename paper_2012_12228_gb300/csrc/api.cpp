@@ -44,10 +44,28 @@ void free_all(ftq_ctx* c) {
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
                     c->tab.hf, c->phi32, c->xbuf, c->xsum, c->pc_w, c->pc_cnt, c->pc_parent, c->pc_pairs,
-                    c->sq_walker, c->sq_w, c->sq_out, c->Yf};
+                    c->sq_walker, c->sq_w, c->sq_out, c->Yf, c->tab.eplus, c->trk, c->trk_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
+
+// A member of a batch runs on the batch's private stream, while the caller
+// hands in buffers that live on its own stream.  A call on a member that
+// reads or writes caller device memory therefore waits for the caller's
+// stream before its work and makes the caller's stream wait for that work
+// after it.  Nothing happens for a stand-alone context (one stream).
+struct CallerOrder {
+    ftq_ctx* c;
+    explicit CallerOrder(ftq_ctx* c_) : c(c_) { link(c->caller_stream, c->stream); }
+    ~CallerOrder() { link(c->stream, c->caller_stream); }
+    void link(cudaStream_t from, cudaStream_t to) {
+        if (!c || !c->member) return;
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return;
+        if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0);
+        cudaEventDestroy(ev);
+    }
+};
 
 }  // namespace
 
@@ -162,6 +180,11 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         }
         chk(upload(c, &c->tab.hf, hf));
         chk(upload(c, &c->tab.qcube, s.qcube));
+        std::vector<int> eplus;                 // pairs of the odd (+Q) slots
+        for (int sl = 1; sl < c->nslot; sl += 2)
+            for (int e = s.pair_ptr[sl]; e < s.pair_ptr[sl + 1]; ++e) eplus.push_back(e);
+        c->tab.neplus = (int)eplus.size();
+        chk(upload(c, &c->tab.eplus, eplus));
     }
     if (e == cudaSuccess && opts->precision == FTQ_MIXED) {
         if (!ftq::tc_supported(M)) {
@@ -187,6 +210,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
 int ftq_reset(ftq_ctx* c) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
     c->resampled = false;
+    c->trk_n = 0;
     cudaError_t e = ftq::launch_init_walkers(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "reset");
     return FTQ_OK;
@@ -194,6 +218,7 @@ int ftq_reset(ftq_ctx* c) {
 
 int ftq_propagate_slices(ftq_ctx* c, int n_slices, const double* fields_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (n_slices < 0) return fail(c, FTQ_EINVAL, "n_slices must be >= 0");
     if (c->k + n_slices > c->sys.n_slices)
         return fail(c, FTQ_EINVAL, "propagation would pass tau = beta; call ftq_reset first");
@@ -219,6 +244,7 @@ int ftq_propagate_slices(ftq_ctx* c, int n_slices, const double* fields_dev) {
         if (e == cudaSuccess && c->opts.stabilise_every > 0 && k % c->opts.stabilise_every == 0)
             e = ftq::launch_qrcp(c);
         if (e == cudaSuccess) e = ftq::launch_green(c, k, true);
+        if (e == cudaSuccess && c->track_every > 0 && k % c->track_every == 0) e = ftq::launch_slice_estimate(c, k);
         if (e != cudaSuccess) return cuda_fail(c, e, "propagate");
         c->k = k;
     }
@@ -227,6 +253,7 @@ int ftq_propagate_slices(ftq_ctx* c, int n_slices, const double* fields_dev) {
 
 int ftq_fields(ftq_ctx* c, int first_slice, int n_slices, double* out_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!out_dev) return fail(c, FTQ_EINVAL, "out_dev must not be NULL");
     if (first_slice < 0 || n_slices < 0 || first_slice + n_slices > c->sys.n_slices)
         return fail(c, FTQ_EINVAL, "slice window outside [0, n)");
@@ -239,6 +266,7 @@ int ftq_fields(ftq_ctx* c, int first_slice, int n_slices, double* out_dev) {
 
 int ftq_structure_factor(ftq_ctx* c, double* out_host, void* per_walker_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
     if (!c->members.empty()) return fail(c, FTQ_EINVAL, "evaluate the members of a batch one by one");
     cudaError_t e = ftq::launch_structure_factor(c, static_cast<double*>(per_walker_dev));
@@ -252,6 +280,7 @@ int ftq_structure_factor(ftq_ctx* c, double* out_host, void* per_walker_dev) {
 
 int ftq_pair_branch(ftq_ctx* c, const double* draws_host, int* parent_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!draws_host) return fail(c, FTQ_EINVAL, "draws_host must not be NULL");
     if (!c->members.empty()) return fail(c, FTQ_EINVAL, "branch the members of a batch one by one");
     if (c->opts.constraint == FTQ_FREE) return fail(c, FTQ_EINVAL, "pair branching acts on phaseless weights");
@@ -266,6 +295,7 @@ int ftq_pair_branch(ftq_ctx* c, const double* draws_host, int* parent_dev) {
 
 int ftq_population_control(ftq_ctx* c, double xi, int* parent_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!c->members.empty()) return fail(c, FTQ_EINVAL, "comb the members of a batch one by one");
     if (!(xi >= 0.0 && xi < 1.0)) return fail(c, FTQ_EINVAL, "xi must lie in [0, 1)");
     if (c->opts.constraint == FTQ_FREE) return fail(c, FTQ_EINVAL, "the comb acts on phaseless weights");
@@ -285,6 +315,7 @@ int ftq_stabilise(ftq_ctx* c) {
 
 int ftq_green(ftq_ctx* c, void* G_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!G_dev) return fail(c, FTQ_EINVAL, "G_dev must not be NULL");
     cudaError_t e = ftq::launch_copy_green(c, reinterpret_cast<double2*>(G_dev));
     if (e != cudaSuccess) return cuda_fail(c, e, "green");
@@ -293,6 +324,7 @@ int ftq_green(ftq_ctx* c, void* G_dev) {
 
 int ftq_estimators(ftq_ctx* c, double* out_host, double* per_walker_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
     cudaError_t e = ftq::launch_estimators(c, per_walker_dev);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, c->red, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream);
@@ -301,8 +333,41 @@ int ftq_estimators(ftq_ctx* c, double* out_host, double* per_walker_dev) {
     return FTQ_OK;
 }
 
+int ftq_track_estimates(ftq_ctx* c, int every) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (every < 0) return fail(c, FTQ_EINVAL, "every must be >= 0");
+    if (!c->members.empty()) return fail(c, FTQ_EINVAL, "track the members of a batch one by one");
+    if (every > 0 && !c->trk) {
+        const size_t rows = (size_t)c->sys.n_slices;
+        cudaError_t e = dalloc(c, &c->trk, 8 * rows);
+        if (e == cudaSuccess) e = dalloc(c, &c->trk_out, 8 * (rows + 1));
+        if (e != cudaSuccess) {
+            if (c->trk) cudaFree(c->trk);
+            c->trk = nullptr;
+            return fail(c, e == cudaErrorMemoryAllocation ? FTQ_ENOMEM : FTQ_ECUDA, "slice estimate record");
+        }
+    }
+    c->track_every = every;
+    return FTQ_OK;
+}
+
+int ftq_slice_estimates(ftq_ctx* c, double* out_host, int capacity) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!out_host || capacity < 0) return fail(c, FTQ_EINVAL, "out_host must not be NULL and capacity >= 0");
+    if (!c->trk) return fail(c, FTQ_EINVAL, "no slice estimates recorded: call ftq_track_estimates first");
+    const int rows = c->trk_n < capacity ? c->trk_n : capacity;
+    cudaError_t e = ftq::launch_slice_summary(c, c->trk_out, rows);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, c->trk_out, sizeof(double) * 8 * (size_t)(rows + 1), cudaMemcpyDeviceToHost,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slice estimates");
+    return FTQ_OK;
+}
+
 int ftq_mu_grad(ftq_ctx* c, double* out_host, double* per_walker_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
     if (c->k != c->sys.n_slices)
         return fail(c, FTQ_EINVAL, "the mu derivative is accumulated over a whole path: propagate to tau = beta first");
@@ -318,6 +383,7 @@ int ftq_mu_grad(ftq_ctx* c, double* out_host, double* per_walker_dev) {
 
 int ftq_weights(ftq_ctx* c, double* out_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    CallerOrder order(c);
     if (!out_dev) return fail(c, FTQ_EINVAL, "out_dev must not be NULL");
     cudaError_t e = cudaMemcpy2DAsync(out_dev, sizeof(double) * 8, c->wstate, sizeof(double) * ftq::WSTRIDE,
                                       sizeof(double) * 8, c->W, cudaMemcpyDeviceToDevice, c->stream);

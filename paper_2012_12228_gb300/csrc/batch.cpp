@@ -90,6 +90,8 @@ int ftq_init_batch(ftq_ctx** out, int nsys, const ftq_system* systems, const ftq
             ftq_destroy(b);
             return bfail(nullptr, rc, why);
         }
+        m->member = true;
+        m->caller_stream = reinterpret_cast<cudaStream_t>(opts->cuda_stream);
         b->members.push_back(m);
     }
     e = ftq::tc_batch_items(b);

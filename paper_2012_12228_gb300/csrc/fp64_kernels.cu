@@ -1,7 +1,7 @@
 // Complex128 kernels of the walker slice: force bias and HS fields, the
 // Taylor-Horner application of B to the chain, Householder QRCP
-// stabilisation, the two-sided stable Green's function with ln det and the
-// phaseless weight, and the UEG estimators.  One walker per thread block
+// stabilisation, and the two-sided stable Green's function with ln det and
+// the phaseless weight (the estimators are in estimators.cu).  One walker per thread block
 // for the factorisations; tiled batched GEMM for the chain.
 #include <cmath>
 
@@ -444,96 +444,6 @@ __global__ void k_green(const double2* __restrict__ Y, const double2* __restrict
     }
 }
 
-// ---------------------------------------------------------------- estimators
-// P = I - G^T.  N = 2 tr P, E_1 = sum |K|^2 P_KK, rho_Q = sum over pairs of
-// P; Gamma part sum_q 4 v_q rho_q rho_-q; exchange part
-// -sum_Q v_Q sum_{(a,d),(b,c) in pairs(Q)} P_ab P_cd.
-__device__ __forceinline__ double2 pel(const double2* Gw, int M, int a, int b) {
-    double2 g = Gw[(long)b * M + a];
-    return make_double2((a == b ? 1.0 : 0.0) - g.x, -g.y);
-}
-
-__global__ void k_estimators(const double2* __restrict__ G, const double* __restrict__ ws,
-                             double* __restrict__ est, const int* __restrict__ pptr,
-                             const int* __restrict__ pa, const int* __restrict__ pb,
-                             const uint16_t* __restrict__ vidx, const double* __restrict__ vq,
-                             const double* __restrict__ ksq, int M, int nqh, double E_M) {
-    extern __shared__ unsigned char smem_raw[];
-    double2* rho = reinterpret_cast<double2*>(smem_raw);     // [2 nqh + 1]
-    __shared__ double2 shc[32];
-    const int w = blockIdx.x;
-    const double2* Gw = G + (long)w * M * M;
-    const int nt = blockDim.x;
-    const int nslot = 2 * nqh + 1;
-    for (int sl = 1 + threadIdx.x; sl < nslot; sl += nt) {
-        double2 r = make_double2(0.0, 0.0);
-        for (int e = pptr[sl]; e < pptr[sl + 1]; ++e) r = r + pel(Gw, M, pa[e], pb[e]);
-        rho[sl] = r;
-    }
-    __syncthreads();
-    double2 nsum = make_double2(0.0, 0.0), e1 = make_double2(0.0, 0.0), e2 = make_double2(0.0, 0.0);
-    for (int a = threadIdx.x; a < M; a += nt) {
-        double2 p = pel(Gw, M, a, a);
-        nsum = nsum + p * 2.0;
-        e1 = e1 + p * ksq[a];
-    }
-    for (int q = threadIdx.x; q < nqh; q += nt) e2 = e2 + cmul(rho[1 + 2 * q], rho[2 + 2 * q]) * (4.0 * vq[q]);
-    const int npair = pptr[nslot];
-    for (int e = threadIdx.x; e < npair; e += nt) {
-        const int a = pa[e], d = pb[e];
-        const int sl = vidx[(long)a * M + d];
-        double2 lam = make_double2(0.0, 0.0);
-        for (int f = pptr[sl]; f < pptr[sl + 1]; ++f) lam = cfma(pel(Gw, M, a, pa[f]), pel(Gw, M, pb[f], d), lam);
-        e2 = e2 - lam * vq[(sl - 1) >> 1];
-    }
-    nsum = block_sum(nsum, shc);
-    e1 = block_sum(e1, shc);
-    e2 = block_sum(e2, shc);
-    if (threadIdx.x == 0) {
-        const double* s = ws + (long)WSTRIDE * w;
-        double* o = est + (long)WSTRIDE * w;
-        o[0] = s[0]; o[1] = s[1]; o[2] = s[2];
-        o[3] = E_M + e1.x + e2.x; o[4] = e1.y + e2.y;
-        o[5] = nsum.x; o[6] = nsum.y; o[7] = 0.0;
-    }
-}
-
-// sum_w of w, wE, wN with w = exp(ln|w| - s) e^{i arg w}, s = max ln|w| (alive)
-__global__ void k_reduce_walkers(const double* __restrict__ est, double* __restrict__ red, int W) {
-    __shared__ double shv[32];
-    __shared__ int shi[32];
-    __shared__ double2 shc[32];
-    double best = -INFINITY;
-    int bi = W;
-    for (int w = threadIdx.x; w < W; w += blockDim.x)
-        if (est[(long)WSTRIDE * w + 2] > 0.5 && isfinite(est[(long)WSTRIDE * w]) && est[(long)WSTRIDE * w] > best) {
-            best = est[(long)WSTRIDE * w];
-            bi = w;
-        }
-    int wm = block_argmax(best, bi, shv, shi);
-    double s = wm < W ? est[(long)WSTRIDE * wm] : 0.0;
-    double2 sw = make_double2(0.0, 0.0), swe = sw, swn = sw;
-    double nal = 0.0;
-    for (int w = threadIdx.x; w < W; w += blockDim.x) {
-        const double* o = est + (long)WSTRIDE * w;
-        if (o[2] <= 0.5 || !isfinite(o[0])) continue;     // a non-finite ln|w| weighs 0
-        double m = exp(o[0] - s);
-        double2 ww = make_double2(m * cos(o[1]), m * sin(o[1]));
-        sw = sw + ww;
-        swe = swe + cmul(ww, make_double2(o[3], o[4]));
-        swn = swn + cmul(ww, make_double2(o[5], o[6]));
-        nal += 1.0;
-    }
-    sw = block_sum(sw, shc);
-    swe = block_sum(swe, shc);
-    swn = block_sum(swn, shc);
-    nal = block_sum(nal, shv);
-    if (threadIdx.x == 0) {
-        red[0] = sw.x; red[1] = sw.y; red[2] = swe.x; red[3] = swe.y;
-        red[4] = swn.x; red[5] = swn.y; red[6] = s; red[7] = nal;
-    }
-}
-
 int fact_threads(int M) {
     int t = ((M + 31) / 32) * 32;
     return t > 1024 ? 1024 : (t < 32 ? 32 : t);
@@ -647,28 +557,6 @@ cudaError_t launch_green(ftq_ctx* c, int k, bool update) {
     // the modified overlap ends with the physical G(beta) and the ratio r
     if (e == cudaSuccess && k == c->sys.n_slices && c->opts.overlap == FTQ_OVERLAP_MODIFIED)
         e = launch_green64(c, c->Y, k, update, true);
-    return e;
-}
-
-cudaError_t launch_estimators(ftq_ctx* c, double* per_walker) {
-    const int M = c->M, nqh = c->sys.nq_half;
-    if (!c->g64_valid) {
-        cudaError_t e0 = mixed_sync_g64(c);
-        if (e0 != cudaSuccess) return e0;
-    }
-    size_t sm = sizeof(double2) * (2 * nqh + 1);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_estimators, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    LaunchScope ls(c, FTQ_K_ESTIMATORS);
-    k_estimators<<<c->W, 256, sm, c->stream>>>(c->G, c->wstate, c->est, c->tab.pair_ptr, c->tab.pair_a,
-                                               c->tab.pair_b, c->tab.vidx, c->tab.vq, c->tab.ksq, M, nqh,
-                                               c->sys.E_M);
-    c->launches[FTQ_K_ESTIMATORS] += 1;
-    k_reduce_walkers<<<1, 256, 0, c->stream>>>(c->est, c->red, c->W);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (per_walker)
-        e = cudaMemcpy2DAsync(per_walker, sizeof(double) * 8, c->est, sizeof(double) * WSTRIDE, sizeof(double) * 8,
-                              c->W, cudaMemcpyDeviceToDevice, c->stream);
     return e;
 }
 

@@ -65,6 +65,8 @@ struct DevTables {
     int* pk = nullptr;            // packed basis coordinates [M]
     float2* hf = nullptr;         // h as float pairs (hi, lo) [M]
     uint16_t* qcube = nullptr;    // difference -> slot [S^3]
+    int* eplus = nullptr;         // the pairs of the half-space transfers (odd slots)
+    int neplus = 0;
 };
 
 }  // namespace ftq
@@ -105,6 +107,10 @@ struct ftq_ctx {
     cudaGraphExec_t gexec = nullptr;
     bool use_graph = true;
     bool owns_stream = false;
+    // a batch member runs on the batch's private stream; calls that read or
+    // write caller memory are ordered against the caller's stream
+    bool member = false;
+    cudaStream_t caller_stream = nullptr;
     double* xbuf = nullptr;       // one slice of internally drawn fields      [W][N_alpha]
     double2* DR = nullptr;        // D_R                                       [W][M]
     double2* phi = nullptr;       // V generator table per walker              [W][nslot]
@@ -126,6 +132,11 @@ struct ftq_ctx {
     double* wstate = nullptr;     // [W][WSTRIDE] per-walker state (layout above)
     double* est = nullptr;        // [W][WSTRIDE] per-walker estimators
     double* red = nullptr;        // [16] reduced sums (estimators, mu derivative)
+    // time-slice estimates: every track_every-th slice, records {k, E_k, N_k, alive, sum w, scale}
+    int track_every = 0;
+    int trk_n = 0;
+    double* trk = nullptr;        // [n_slices][8]
+    double* trk_out = nullptr;    // [n_slices + 1][8] summary read by ftq_slice_estimates
     int* status = nullptr;        // latched numeric status
     size_t bytes = 0;
     std::string err;
@@ -186,6 +197,9 @@ cudaError_t launch_chain(ftq_ctx* c);
 cudaError_t launch_qrcp(ftq_ctx* c);
 cudaError_t launch_green(ftq_ctx* c, int k, bool update_weights);
 cudaError_t launch_estimators(ftq_ctx* c, double* per_walker);
+// Estimators of slice k into the next slice record (estimators.cu).
+cudaError_t launch_slice_estimate(ftq_ctx* c, int k);
+cudaError_t launch_slice_summary(ftq_ctx* c, double* out_dev, int rows);
 cudaError_t launch_copy_green(ftq_ctx* c, double2* out);
 // complex128 factorisations on explicit buffers
 cudaError_t launch_qrcp64(ftq_ctx* c, const double2* Yin, double2* Qout);

@@ -7,10 +7,16 @@
 // stabilisation): C Pi has decreasing column norms, Y is well conditioned
 // (a few B's times a unitary matrix) and the grading sits in D_R, so an
 // unpivoted Householder QR of C Pi separates the scales like QRCP does.
+// A column scaling only rescales R: with D' = Pi^T D_R Pi and
+// Y Pi = Q R_Y, C Pi = Y Pi D' = Q (R_Y D').  So the reflectors and Q come
+// from Y Pi alone, which is FP32-accurate, and are computed in FP32; the
+// scales D_R = diag(R_Y) D', U = D^-1 R and the update of T^-1 stay in FP64.
 //
-//   k_qr_prepiv64 (FP64, one block per walker): norms, sort, C Pi, Householder
-//       QR, D <- diag R, U = D^-1 R, T^-1 <- T^-1 Pi^T U^-1, permutation parity;
-//       the reflectors are also written in FP32, one reflector per row.
+//   k_prepiv32 (one block per walker): norms of C in FP64, ranks, parity,
+//       D', and A = Y Pi (FP32, row-major).
+//   k_qr32 (one block per walker): blocked Householder QR of A in FP32
+//       (compact WY panels of NB columns); R_Y in A, reflectors and tau out.
+//   k_tinv64 (FP64, one block per walker): D_R, U and T^-1 <- T^-1 Pi U^-1.
 //   k_form_q32 (FP32, one block per walker and 32-column panel): Q = H_0 ...
 //       H_{M-1} applied to the identity panel in shared memory, written into
 //       the chain planes as the new Y.
@@ -26,97 +32,42 @@ namespace {
 constexpr int QP = 32;   // columns per Q panel
 constexpr int NBJ = 2;   // columns per block of the T^-1 update
 
-__device__ double bsum_d(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double acc = sh[0];
-        for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i) acc += sh[i];
-        sh[0] = acc;
-    }
-    __syncthreads();
-    double r = sh[0];
-    __syncthreads();
-    return r;
-}
-
-// (launch bounds: four 288-thread blocks per SM; measured faster than three
-// uncapped blocks or smaller blocks at M = 257)
-// Block sum of a complex value; every thread returns the total.
-__device__ double2 bsum_c(double2 v, double2* sh) {
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double2 acc = sh[0];
-    for (int i = 1; i < (int)((blockDim.x + 31) >> 5); ++i) acc = acc + sh[i];
-    __syncthreads();
-    return acc;
-}
-
-// Householder reflector of column j from its squared norm s (rows >= j):
-// beta = -|x| x_j/|x_j| replaces C[j][j]; u_j = x_j - beta, tau = 2/(u^H u).
-__device__ void reflector_head(double2* C, double* htau_w, int* status, int M, int j, double s, double2* u0,
-                               double* tau) {
-    const double2 al = C[(long)j * M + j];
-    const double sig = sqrt(s);
-    const double aa = sqrt(abs2(al));
-    const double2 beta = aa > 0.0 ? al * (-sig / aa) : make_double2(-sig, 0.0);
-    const double uhu = 2.0 * sig * (sig + aa);
-    *u0 = al - beta;
-    *tau = uhu > 0.0 ? 2.0 / uhu : 0.0;
-    htau_w[j] = *tau;
-    C[(long)j * M + j] = beta;
-    if (!(sig > 0.0)) atomicOr(status, 1);
-}
-
-__global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict__ Ypl, double2* __restrict__ work,
-                              double2* __restrict__ work2, double2* __restrict__ DR, double2* __restrict__ Tinv,
-                              float2* __restrict__ VT, double* __restrict__ htau, double* __restrict__ xsum,
-                              double* __restrict__ ws,
-                              int* __restrict__ status, int M, Planes P, size_t wstride) {
+// ---------------------------------------------------------------- S1: pre-pivoting
+// Column norms of C = Y D_R (FP64 sums of the FP32 chain, a warp per column),
+// the rank of every column (descending norm, ties to the lower index), the
+// permutation's parity, D' = D_R Pi, and the permuted chain A = Y Pi written
+// row-major in FP32 through 32 x 33 shared tiles (columns of Y are read
+// contiguously, rows of A written contiguously).
+__global__ void __launch_bounds__(256) k_prepiv32(const float* __restrict__ Ypl, float2* __restrict__ A,
+                                                 const double2* __restrict__ DR, double2* __restrict__ Dp,
+                                                 int* __restrict__ permg, double* __restrict__ ws,
+                                                 int* __restrict__ status, int M, Planes P, size_t wstride) {
     extern __shared__ unsigned char smem_raw[];
-    double* ub = reinterpret_cast<double*>(smem_raw);      // [M][NBJ][3] U block of the T^-1 update
-    double* cn = ub + 3 * NBJ * M;                         // [M] column norms of C
-    int* perm = reinterpret_cast<int*>(cn + M);            // [M] C Pi column j = C column perm[j]
+    double* cn = reinterpret_cast<double*>(smem_raw);                  // [M]
+    float2* tile = reinterpret_cast<float2*>(cn + M);                 // [32][33]
+    int* perm = reinterpret_cast<int*>(tile + 32 * 33);               // [M]
     unsigned char* seen = reinterpret_cast<unsigned char*>(perm + M);   // [M]
-    __shared__ double shd[32];
-    __shared__ double2 piv_u0, piv_u1, shc2[32];
-    __shared__ double piv_tau, piv_tau1;
-    __shared__ int parity;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int w = blockIdx.x;
-    const long off = (long)w * M * M;
-    double2* C = work + off;
-    double2* XT = work2 + off;
-    double2* Ti = Tinv + off;
-    double2* Dw = DR + (long)w * M;
-    float2* V = VT + off;
     const float* Yw = Ypl + wstride * w;
-
-    // column norms of C = Y D_R, then the rank of every column (descending
-    // norm, ties to the lower index)
-    for (int c = tid; c < M; c += nt) {
-        double s = 0.0;
-        for (int i = 0; i < M; ++i) {
-            float2 y = P.load(Yw, i, c);
-            s += (double)y.x * y.x + (double)y.y * y.y;
+    const double2* Dw = DR + (long)w * M;
+    for (int c = warp; c < M; c += nw) {
+        double sum = 0.0;
+        for (int i = lane; i < M; i += 32) {
+            const float2 y = P.load(Yw, i, c);
+            sum += (double)y.x * y.x + (double)y.y * y.y;
         }
-        double v = s * abs2(Dw[c]);
-        // a NaN norm would compare false both ways and give two columns one
-        // rank (leaving an entry of perm unset); rank it last and latch
-        if (v != v) {
-            v = -INFINITY;
-            atomicOr(status, 1);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+        if (lane == 0) {
+            double v = sum * abs2(Dw[c]);
+            // a NaN norm would compare false both ways and give two columns one
+            // rank (leaving an entry of perm unset); rank it last and latch
+            if (v != v) {
+                v = -INFINITY;
+                atomicOr(status, 1);
+            }
+            cn[c] = v;
         }
-        cn[c] = v;
     }
     __syncthreads();
     for (int c = tid; c < M; c += nt) {
@@ -135,103 +86,253 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
             ++cycles;
             for (int x = c; !seen[x]; x = perm[x]) seen[x] = 1;
         }
-        parity = (M - cycles) & 1;
+        double* st = ws + (long)WSTRIDE * w;
+        st[7] = (double)(((int)st[7]) ^ ((M - cycles) & 1));
     }
-    for (long e = tid; e < (long)M * M; e += nt) {
-        const int i = (int)(e / M), j = (int)(e % M);
-        const int src = perm[j];
-        const float2 y = P.load(Yw, i, src);
-        C[e] = cmul(make_double2(y.x, y.y), Dw[src]);
+    for (int j = tid; j < M; j += nt) {
+        permg[(long)w * M + j] = perm[j];
+        Dp[(long)w * M + j] = Dw[perm[j]];
     }
-    __syncthreads();
+    float2* Aw = A + (long)w * M * M;
+    const int nt32 = (M + 31) / 32;
+    for (int t = 0; t < nt32 * nt32; ++t) {
+        const int i0 = (t / nt32) * 32, j0 = (t % nt32) * 32;
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += nt) {
+            const int jj = e >> 5, ii = e & 31;                // read column perm[j0 + jj], rows i0 + ii
+            const int i = i0 + ii, j = j0 + jj;
+            tile[jj * 33 + ii] = (i < M && j < M) ? P.load(Yw, i, perm[j]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += nt) {
+            const int ii = e >> 5, jj = e & 31;                // write row i0 + ii, columns j0 + jj
+            const int i = i0 + ii, j = j0 + jj;
+            if (i < M && j < M) Aw[(long)i * M + j] = tile[jj * 33 + ii];
+        }
+    }
+}
 
-    // Householder QR of C Pi, two reflectors per pass over the trailing
-    // columns: H_j is applied to column j + 1 first and u_{j+1} formed; then
-    // every later column x takes both in one read pass (d1 = u_j^H x,
-    // d2 = u_{j+1}^H x) and one write pass, x -= a1 u_j + a2 u_{j+1} with
-    // a1 = tau_j d1 and a2 = tau_{j+1} (d2 - a1 u_{j+1}^H u_j).
-    for (int j = 0; j < M; j += 2) {
-        double s = 0.0;
-        for (int r = j + tid; r < M; r += nt) s += abs2(C[(long)r * M + j]);
-        s = bsum_d(s, shd);
-        if (tid == 0) reflector_head(C, htau + (long)w * M, status, M, j, s, &piv_u0, &piv_tau);
+// ---------------------------------------------------------------- S2: FP32 blocked Householder QR
+// Householder QR of A = Y Pi (M x M, row-major, FP32), one block per walker,
+// NB-column panels.  A panel (rows j0.., NB columns) is factorised in shared
+// memory (a reflector per column: beta = -|x| x_0/|x_0| replaces the
+// diagonal, u = x - beta e_0, tau = 1/(|x| (|x| + |x_0|)), H = I - tau u u^H
+// Hermitian); T of the compact form H_0 ... H_{nb-1} = I - V T V^H is built
+// from the Gram matrix of V; the trailing columns then take all nb
+// reflectors at once, A <- A - V T^H (V^H A), one column per thread, V read
+// from shared memory (the same row for every thread: a broadcast), so each
+// column is read twice and written once per panel.  Outputs: R in the upper
+// triangle of A, the reflectors as rows VT[j][r] (r >= j, u_0 at r = j) and
+// tau in FP64 for the Q panels.
+template <int NB>
+__global__ void __launch_bounds__(256, 1) k_qr32(float2* __restrict__ A, float2* __restrict__ VT,
+                                                double* __restrict__ htau, int* __restrict__ status, int M) {
+    extern __shared__ unsigned char smem_raw[];
+    float2* V = reinterpret_cast<float2*>(smem_raw);        // [M][NB]  panel, then the reflectors
+    float2* Yt = V + (size_t)M * NB;                        // [M][NB]  V T^H
+    __shared__ float2 T[NB][NB + 1];
+    __shared__ float2 Sg[NB][NB + 1];
+    __shared__ float tau_s[NB];
+    __shared__ float2 beta_s[NB];
+    __shared__ float red[32];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int w = blockIdx.x;
+    float2* Aw = A + (long)w * M * M;
+    float2* Vw = VT + (long)w * M * M;
+    double* tw = htau + (long)w * M;
+    for (int e = tid; e < NB * (NB + 1); e += nt) (&T[0][0])[e] = make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < M; j0 += NB) {
+        const int nb = min(NB, M - j0), rows = M - j0;
+        for (int e = tid; e < rows * NB; e += nt) {
+            const int r = e / NB, c = e % NB;
+            V[e] = c < nb ? Aw[(long)(j0 + r) * M + j0 + c] : make_float2(0.f, 0.f);
+        }
         __syncthreads();
-        const double2 uj = piv_u0;           // u_j[j]; u_j[r] = C[r][j] below
-        const double tj = piv_tau;
-        // reflector j in FP32 for the Q panels: V[j][r] = u_r, r >= j
-        for (int r = j + tid; r < M; r += nt) {
-            const double2 u = r == j ? uj : C[(long)r * M + j];
-            V[(long)j * M + r] = make_float2((float)u.x, (float)u.y);
-        }
-        if (j + 1 >= M) break;
-        // H_j on column j + 1
-        double2 d = make_double2(0.0, 0.0);
-        for (int r = j + tid; r < M; r += nt) {
-            const double2 u = r == j ? uj : C[(long)r * M + j];
-            d = cfma(conj(u), C[(long)r * M + j + 1], d);
-        }
-        const double2 a = bsum_c(d, shc2) * tj;
-        for (int r = j + tid; r < M; r += nt) {
-            const double2 u = r == j ? uj : C[(long)r * M + j];
-            C[(long)r * M + j + 1] = cfms(u, a, C[(long)r * M + j + 1]);
-        }
-        __syncthreads();
-        // reflector j + 1
-        s = 0.0;
-        for (int r = j + 1 + tid; r < M; r += nt) s += abs2(C[(long)r * M + j + 1]);
-        s = bsum_d(s, shd);
-        if (tid == 0) reflector_head(C, htau + (long)w * M, status, M, j + 1, s, &piv_u1, &piv_tau1);
-        __syncthreads();
-        const double2 u1 = piv_u1;           // u_{j+1}[j+1]; u_{j+1}[r] = C[r][j+1] below
-        const double t1 = piv_tau1;
-        for (int r = j + 1 + tid; r < M; r += nt) {
-            const double2 u = r == j + 1 ? u1 : C[(long)r * M + j + 1];
-            V[(long)(j + 1) * M + r] = make_float2((float)u.x, (float)u.y);
-        }
-        // g = u_{j+1}^H u_j (rows >= j + 1)
-        double2 gp = make_double2(0.0, 0.0);
-        for (int r = j + 1 + tid; r < M; r += nt) {
-            const double2 u = r == j + 1 ? u1 : C[(long)r * M + j + 1];
-            gp = cfma(conj(u), C[(long)r * M + j], gp);
-        }
-        const double2 g = bsum_c(gp, shc2);
-        const double2 uj1 = C[(long)(j + 1) * M + j];    // u_j[j+1]
-        for (int c = j + 2 + tid; c < M; c += nt) {
-            const double2 x0 = C[(long)j * M + c], x1 = C[(long)(j + 1) * M + c];
-            double2 d1 = cfma(conj(uj1), x1, cmul(conj(uj), x0));
-            double2 d2 = cmul(conj(u1), x1);
-            for (int r = j + 2; r < M; ++r) {
-                const double2 x = C[(long)r * M + c];
-                d1 = cfma(conj(C[(long)r * M + j]), x, d1);
-                d2 = cfma(conj(C[(long)r * M + j + 1]), x, d2);
+        // unblocked factorisation of the panel
+        for (int c = 0; c < nb; ++c) {
+            float s = 0.f;
+            for (int r = c + tid; r < rows; r += nt) {
+                const float2 x = V[r * NB + c];
+                s = fmaf(x.x, x.x, fmaf(x.y, x.y, s));
             }
-            const double2 a1 = d1 * tj;
-            const double2 a2 = cfms(a1, g, d2) * t1;
-            C[(long)j * M + c] = cfms(uj, a1, x0);
-            C[(long)(j + 1) * M + c] = cfms(u1, a2, cfms(uj1, a1, x1));
-            for (int r = j + 2; r < M; ++r) {
-                double2 x = C[(long)r * M + c];
-                x = cfms(C[(long)r * M + j], a1, x);
-                x = cfms(C[(long)r * M + j + 1], a2, x);
-                C[(long)r * M + c] = x;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) red[warp] = s;
+            __syncthreads();
+            if (tid == 0) {
+                float tot = 0.f;
+                for (int q = 0; q < nw; ++q) tot += red[q];
+                const float2 al = V[c * NB + c];
+                const float sig = sqrtf(tot);
+                const float aa = sqrtf(al.x * al.x + al.y * al.y);
+                const float2 be = aa > 0.f ? make_float2(-sig * al.x / aa, -sig * al.y / aa) : make_float2(-sig, 0.f);
+                const float uhu = sig * (sig + aa);
+                tau_s[c] = uhu > 0.f ? 1.f / uhu : 0.f;
+                beta_s[c] = be;
+                V[c * NB + c] = make_float2(al.x - be.x, al.y - be.y);     // u_0
+                if (!(sig > 0.f)) atomicOr(status, 1);
+            }
+            __syncthreads();
+            const float tc = tau_s[c];
+            for (int c2 = c + 1 + warp; c2 < nb; c2 += nw) {
+                float dx = 0.f, dy = 0.f;                              // u^H x
+                for (int r = c + lane; r < rows; r += 32) {
+                    const float2 u = V[r * NB + c], x = V[r * NB + c2];
+                    dx = fmaf(u.x, x.x, fmaf(u.y, x.y, dx));
+                    dy = fmaf(u.x, x.y, fmaf(-u.y, x.x, dy));
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    dx += __shfl_xor_sync(0xffffffffu, dx, o);
+                    dy += __shfl_xor_sync(0xffffffffu, dy, o);
+                }
+                dx *= tc;
+                dy *= tc;
+                for (int r = c + lane; r < rows; r += 32) {
+                    const float2 u = V[r * NB + c];
+                    float2 x = V[r * NB + c2];
+                    x.x = fmaf(-u.x, dx, fmaf(u.y, dy, x.x));
+                    x.y = fmaf(-u.x, dy, fmaf(-u.y, dx, x.y));
+                    V[r * NB + c2] = x;
+                }
+            }
+            __syncthreads();
+        }
+        // R rows of the panel and the reflectors out; V keeps only the reflectors
+        for (int e = tid; e < rows * NB; e += nt) {
+            const int r = e / NB, c = e % NB;
+            if (c >= nb) continue;
+            const float2 v = V[e];
+            if (r < c) {
+                Aw[(long)(j0 + r) * M + j0 + c] = v;                     // R above the diagonal
+                V[e] = make_float2(0.f, 0.f);
+            } else {
+                Vw[(long)(j0 + c) * M + j0 + r] = v;
+                if (r == c) Aw[(long)(j0 + r) * M + j0 + c] = beta_s[c];
+            }
+        }
+        for (int c = tid; c < nb; c += nt) tw[j0 + c] = (double)tau_s[c];
+        __syncthreads();
+        if (j0 + nb >= M) break;
+        // Gram matrix S = V^H V (upper part) and T: T_cc = tau_c,
+        // T[0:c, c] = -tau_c T[0:c, 0:c] S[0:c, c]
+        for (int q = warp; q < nb * nb; q += nw) {
+            const int a = q / nb, b = q % nb;
+            if (a >= b) continue;
+            float sx = 0.f, sy = 0.f;
+            for (int r = b + lane; r < rows; r += 32) {
+                const float2 u = V[r * NB + a], x = V[r * NB + b];
+                sx = fmaf(u.x, x.x, fmaf(u.y, x.y, sx));
+                sy = fmaf(u.x, x.y, fmaf(-u.y, x.x, sy));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+            if (lane == 0) Sg[a][b] = make_float2(sx, sy);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int c = 0; c < nb; ++c) {
+                // lane a < c: T[a][c] = -tau_c sum_{b = a .. c-1} T[a][b] S[b][c]
+                float2 t = make_float2(0.f, 0.f);
+                if (lane < c) {
+                    for (int b = lane; b < c; ++b) {
+                        const float2 x = T[lane][b], y = Sg[b][c];
+                        t.x = fmaf(x.x, y.x, fmaf(-x.y, y.y, t.x));
+                        t.y = fmaf(x.x, y.y, fmaf(x.y, y.x, t.y));
+                    }
+                }
+                __syncwarp();
+                if (lane < c) T[lane][c] = make_float2(-tau_s[c] * t.x, -tau_s[c] * t.y);
+                if (lane == c) T[c][c] = make_float2(tau_s[c], 0.f);
+                if (lane > c && lane < NB) T[lane][c] = make_float2(0.f, 0.f);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // Yt = V T^H: Yt[r][c] = sum_{b >= c} V[r][b] conj(T[c][b])
+        for (int e = tid; e < rows * NB; e += nt) {
+            const int r = e / NB, c = e % NB;
+            float2 t = make_float2(0.f, 0.f);
+            for (int b = c; b < NB; ++b) {
+                const float2 v = V[r * NB + b], x = T[c][b];
+                t.x = fmaf(v.x, x.x, fmaf(v.y, x.y, t.x));
+                t.y = fmaf(v.y, x.x, fmaf(-v.x, x.y, t.y));
+            }
+            Yt[e] = t;
+        }
+        __syncthreads();
+        // trailing columns: w = V^H a, then a <- a - (V T^H) w
+        for (int col = j0 + nb + tid; col < M; col += nt) {
+            float2 wv[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) wv[c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+            for (int r = 0; r < rows; ++r) {
+                const float2 a = Aw[(long)(j0 + r) * M + col];
+                const float2* vr = V + r * NB;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const float2 u = vr[c];                            // conj(u) a
+                    wv[c].x = fmaf(u.x, a.x, fmaf(u.y, a.y, wv[c].x));
+                    wv[c].y = fmaf(u.x, a.y, fmaf(-u.y, a.x, wv[c].y));
+                }
+            }
+#pragma unroll 1
+            for (int r = 0; r < rows; ++r) {
+                float2 a = Aw[(long)(j0 + r) * M + col];
+                const float2* yr = Yt + r * NB;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const float2 u = yr[c];
+                    a.x = fmaf(-u.x, wv[c].x, fmaf(u.y, wv[c].y, a.x));
+                    a.y = fmaf(-u.x, wv[c].y, fmaf(-u.y, wv[c].x, a.y));
+                }
+                Aw[(long)(j0 + r) * M + col] = a;
             }
         }
         __syncthreads();
     }
-    for (int j = tid; j < M; j += nt) Dw[j] = C[(long)j * M + j];
-    __syncthreads();
-    for (long e = tid; e < (long)M * M; e += nt) {
-        const int i = (int)(e / M), c = (int)(e % M);
-        if (c > i) C[e] = cdiv(C[e], C[(long)i * M + i]);
+}
+
+// ---------------------------------------------------------------- S3: FP64 update of the right block
+// From R_Y (upper triangle of A, FP32) and D' (FP64): D_R <- diag(R_Y) D',
+// U = D^-1 R with R = R_Y D', i.e. U_mj = (R_Y[m][j] / R_Y[m][m]) (D'_j / D'_m)
+// in FP64, and T^-1 <- T^-1 Pi U^-1 by the blocked column solve below.
+__global__ void __launch_bounds__(288, 4) k_tinv64(const float2* __restrict__ A, const double2* __restrict__ Dp,
+                                                  const int* __restrict__ permg, double2* __restrict__ work,
+                                                  double2* __restrict__ work2, double2* __restrict__ DR,
+                                                  double2* __restrict__ Tinv, double* __restrict__ xsum,
+                                                  int* __restrict__ status, int M) {
+    extern __shared__ unsigned char smem_raw[];
+    double* ub = reinterpret_cast<double*>(smem_raw);      // [M][NBJ][3] U block of the T^-1 update
+    double2* dinv = reinterpret_cast<double2*>(ub + 3 * NBJ * M);   // [M] 1 / (R_Y[m][m] D'_m)
+    int* perm = reinterpret_cast<int*>(dinv + M);          // [M]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int w = blockIdx.x;
+    const long off = (long)w * M * M;
+    const float2* Aw = A + off;
+    double2* C = work + off;
+    double2* XT = work2 + off;
+    double2* Ti = Tinv + off;
+    const double2* Dpw = Dp + (long)w * M;
+    for (int j = tid; j < M; j += nt) {
+        const float2 r = Aw[(long)j * M + j];
+        const double2 d = cmul(make_double2(r.x, r.y), Dpw[j]);
+        DR[(long)w * M + j] = d;
+        if (!(abs2(d) > 0.0)) atomicOr(status, 1);
+        dinv[j] = cinv(d);
+        perm[j] = permg[(long)w * M + j];
     }
     __syncthreads();
-    // Re U + Im U of the strict upper triangle, kept in the real parts of the
-    // (no longer needed) lower triangle: U[m][j] -> C[j][m].x
+    // U in the strict upper triangle of C, Re U + Im U in the real parts of
+    // the lower triangle: U[m][j] -> C[j][m].x
     for (long e = tid; e < (long)M * M; e += nt) {
-        const int j = (int)(e / M), m = (int)(e % M);
-        if (m < j) {
-            const double2 u = C[(long)m * M + j];
-            C[e].x = u.x + u.y;
+        const int m = (int)(e / M), j = (int)(e % M);
+        if (j > m) {
+            const float2 r = Aw[e];
+            const double2 u = cmul(cmul(make_double2(r.x, r.y), Dpw[j]), dinv[m]);
+            C[e] = u;
+            C[(long)j * M + m].x = u.x + u.y;
         }
     }
     __syncthreads();
@@ -299,10 +400,6 @@ __global__ void __launch_bounds__(288, 4) k_qr_prepiv64(const float* __restrict_
     }
     for (int i = tid; i < M; i += nt)
         for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
-    if (tid == 0) {
-        double* st = ws + (long)WSTRIDE * w;
-        st[7] = (double)(((int)st[7]) ^ parity);
-    }
 }
 
 // Q[:, c0 .. c0+32) = H_0 ... H_{M-1} e_c, accumulated backwards in shared
@@ -374,28 +471,67 @@ __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT,
 
 }  // namespace
 
+int qr_panel_width(int M) {
+    for (int nb = 32; nb > 8; nb >>= 1)
+        if (2 * sizeof(float2) * (size_t)M * nb <= 200 * 1024) return nb;
+    return 8;
+}
+
 cudaError_t launch_qr_prepiv(ftq_ctx* c) {
     const int M = c->M;
     Planes P;
     P.Kp = c->Kp;
     P.part = (size_t)c->LD * 2 * c->Kp;
     const size_t ws = 2 * P.part;
-    int nt = (M + 31) / 32 * 32;
-    nt = nt < 64 ? 64 : (nt > 288 ? 288 : nt);          // the launch bound; every loop strides by nt
-    const size_t sm1 = (3 * NBJ + 1) * sizeof(double) * M + (sizeof(int) + 1) * M + 16;
-    static size_t sm1_set = 48 * 1024;
-    if (sm1 > sm1_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_qr_prepiv64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-        if (e != cudaSuccess) return e;
-        sm1_set = sm1;
-    }
+    cudaError_t e;
     {
         LaunchScope ls(c, FTQ_K_QRCP);
-        k_qr_prepiv64<<<c->W, nt, sm1, c->stream>>>(c->Ypl, c->work, c->work2, c->DR, c->Tinv, c->w2_32, c->htau,
-                                                    c->xsum, c->wstate, c->status, M, P, ws);
+        const size_t sm0 = (sizeof(double) + sizeof(int) + 1) * M + sizeof(float2) * 32 * 33 + 16;
+        static size_t sm0_set = 48 * 1024;
+        if (sm0 > sm0_set) {
+            e = cudaFuncSetAttribute(k_prepiv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
+            if (e != cudaSuccess) return e;
+            sm0_set = sm0;
+        }
+        k_prepiv32<<<c->W, 256, sm0, c->stream>>>(c->Ypl, c->w32, c->DR, c->hh, c->perm, c->wstate, c->status, M,
+                                                  P, ws);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        // FP32 Householder QR: the widest panel (32, 16 or 8 columns) whose two
+        // M x NB shared arrays fit
+        const int nbq = qr_panel_width(M);
+        const size_t smq = 2 * sizeof(float2) * (size_t)M * nbq;
+        static size_t smq_set[3] = {48 * 1024, 48 * 1024, 48 * 1024};
+        const int which = nbq == 32 ? 0 : (nbq == 16 ? 1 : 2);
+        if (smq > smq_set[which]) {
+            e = nbq == 32 ? cudaFuncSetAttribute(k_qr32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq)
+                : nbq == 16 ? cudaFuncSetAttribute(k_qr32<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq)
+                            : cudaFuncSetAttribute(k_qr32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+            if (e != cudaSuccess) return e;
+            smq_set[which] = smq;
+        }
+        if (nbq == 32) k_qr32<32><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
+        else if (nbq == 16) k_qr32<16><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
+        else k_qr32<8><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls(c, FTQ_K_TINV);
+        int nt = (M + 31) / 32 * 32;
+        nt = nt < 64 ? 64 : (nt > 288 ? 288 : nt);          // the launch bound; every loop strides by nt
+        const size_t sm1 = 3 * NBJ * sizeof(double) * M + sizeof(double2) * M + sizeof(int) * M + 16;
+        static size_t sm1_set = 48 * 1024;
+        if (sm1 > sm1_set) {
+            e = cudaFuncSetAttribute(k_tinv64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+            if (e != cudaSuccess) return e;
+            sm1_set = sm1;
+        }
+        k_tinv64<<<c->W, nt, sm1, c->stream>>>(c->w32, c->hh, c->perm, c->work, c->work2, c->DR, c->Tinv, c->xsum,
+                                               c->status, M);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const size_t sm2 = sizeof(float2) * ((size_t)M * QP + M);
     static size_t sm2_set = 48 * 1024;
     if (sm2 > sm2_set) {
