@@ -256,7 +256,8 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     host = gaussian_fields(seed, total * stab, W, na).reshape(total, stab, W, na)
     fields = torch.from_numpy(host).to(dev)
     out = {"M": M, "n_slices": n, "dtau": prop.query_f64("DTAU"), "walkers": W, "stab": stab, "p": p_order,
-           "autotune": None if tuned is None else {"column_tiles": tuned[0], "ms_per_horner_step": tuned[1]}}
+           "autotune": None if tuned is None else {"column_tiles": tuned[0], "ms_per_horner_step": tuned[1],
+                                                   "qr_panel": prop.query("QR_PANEL")}}
 
     for s in range(warmup):
         prop.propagate(fields[s])

@@ -288,6 +288,7 @@ int ftq_slice_estimates(ftq_ctx* ctx, double* out_host, int capacity);
 #define FTQ_Q_NCUT2      5
 #define FTQ_Q_PRECISION  6
 #define FTQ_Q_DEVICE_BYTES 7 /* device bytes owned by the context */
+#define FTQ_Q_QR_PANEL   8   /* panel width of the mixed path's FP32 QR (0: default) */
 int ftq_query(const ftq_ctx* ctx, int key, int64_t* value);
 
 /* Floating-point properties. */
@@ -327,10 +328,11 @@ int ftq_batch_propagate(ftq_ctx* batch, int n_slices, const double* const* field
 
 /* Time the candidate column tilings (1, 2 or 3 column tiles per 64-row
  * block) of the tensor-core chain on the context's own shapes and keep the
- * fastest; for a batch every member is tuned.  choice / ms: nullable host
- * arrays (one entry per system) receiving the chosen tile count and its time
- * per Horner step.  Uses the chain's scratch buffers; walker state is not
- * changed. */
+ * fastest, and likewise the panel width (32, 16 or 8 columns) of the FP32
+ * Householder QR of the stabilisation; for a batch every member is tuned.
+ * choice / ms: nullable host arrays (one entry per system) receiving the
+ * chosen tile count and its time per Horner step.  Uses the scratch buffers
+ * of the chain and of the stabilisation; walker state is not changed. */
 int ftq_autotune(ftq_ctx* ctx, int* choice, float* ms);
 
 /* Kernel classes for launch accounting and timing. */

@@ -11,7 +11,7 @@ import os
 FTQ_FP64, FTQ_MIXED, FTQ_MIXED_SIMT = 0, 1, 2
 FTQ_PHASELESS, FTQ_FREE = 0, 1
 FTQ_OVERLAP_PAPER, FTQ_OVERLAP_MODIFIED = 0, 1
-_Q = dict(M=0, N_ALPHA=1, N_SLICES=2, SLICE=3, WALKERS=4, NCUT2=5, PRECISION=6, DEVICE_BYTES=7)
+_Q = dict(M=0, N_ALPHA=1, N_SLICES=2, SLICE=3, WALKERS=4, NCUT2=5, PRECISION=6, DEVICE_BYTES=7, QR_PANEL=8)
 _F = dict(BETA=0, DTAU=1, MU=2, MU_T=3, L=4, E_M=5)
 
 HERE = os.path.dirname(os.path.abspath(__file__))

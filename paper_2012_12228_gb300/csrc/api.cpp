@@ -431,6 +431,7 @@ int ftq_query(const ftq_ctx* c, int key, int64_t* value) {
         case FTQ_Q_NCUT2: *value = c->sys.ncut2; break;
         case FTQ_Q_PRECISION: *value = c->opts.precision; break;
         case FTQ_Q_DEVICE_BYTES: *value = (int64_t)c->bytes; break;
+        case FTQ_Q_QR_PANEL: *value = c->qr_nb; break;
         default: return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "unknown query key");
     }
     return FTQ_OK;

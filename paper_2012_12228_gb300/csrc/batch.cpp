@@ -169,6 +169,9 @@ int ftq_autotune(ftq_ctx* c, int* choice, float* ms) {
         int best = 1;
         float bms = 0.f;
         cudaError_t e = ftq::tc_autotune(m, &best, &bms);
+        int qnb = 0;
+        float qms = 0.f;
+        if (e == cudaSuccess) e = ftq::qr_autotune(m, &qnb, &qms);
         if (e != cudaSuccess) return bfail(c, FTQ_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
         if (choice) choice[s] = best;
         if (ms) ms[s] = bms;

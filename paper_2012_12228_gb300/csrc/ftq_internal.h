@@ -100,6 +100,7 @@ struct ftq_ctx {
     const float* tmap_buf[3] = {nullptr, nullptr, nullptr};
     int nct = 1;                  // column tiles of the tensor-core chain (autotuned)
     int64_t wait_limit = -1;      // polls per mbarrier wait of the tensor-core chain (-1: default)
+    int qr_nb = 0;                // panel width of the FP32 stabilisation QR (0: widest that fits)
     int4* items = nullptr;        // work list of the tensor-core chain
     int nitems = 0;
     // ragged batch: member systems (owned), CUDA graph of the last propagation
@@ -232,6 +233,7 @@ cudaError_t launch_green32b(ftq_ctx* c, int k);
 
 // Pre-pivoted stabilisation of the mixed chain (qr_mixed.cu).
 cudaError_t launch_qr_prepiv(ftq_ctx* c);
+cudaError_t qr_autotune(ftq_ctx* c, int* best_nb, float* best_ms);
 
 // Tensor-core chain (chain_tc.cu).
 void tc_plan(int M, int nct, int* R, int* NT);

@@ -41,7 +41,8 @@ constexpr int NBJ = 2;   // columns per block of the T^-1 update
 __global__ void __launch_bounds__(256) k_prepiv32(const float* __restrict__ Ypl, float2* __restrict__ A,
                                                  const double2* __restrict__ DR, double2* __restrict__ Dp,
                                                  int* __restrict__ permg, double* __restrict__ ws,
-                                                 int* __restrict__ status, int M, Planes P, size_t wstride) {
+                                                 int* __restrict__ status, int M, Planes P, size_t wstride,
+                                                 int update_parity) {
     extern __shared__ unsigned char smem_raw[];
     double* cn = reinterpret_cast<double*>(smem_raw);                  // [M]
     float2* tile = reinterpret_cast<float2*>(cn + M);                 // [32][33]
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) k_prepiv32(const float* __restrict__ Ypl,
         seen[c] = 0;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && update_parity) {
         // parity of the permutation = (M - number of cycles) mod 2
         int cycles = 0;
         for (int c = 0; c < M; ++c) {
@@ -471,10 +472,83 @@ __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT,
 
 }  // namespace
 
-int qr_panel_width(int M) {
+bool qr_width_fits(int M, int nb) { return 2 * sizeof(float2) * (size_t)M * nb <= 200 * 1024; }
+
+// The context's panel width when it fits (autotuned), else the widest that fits.
+int qr_panel_width(const ftq_ctx* c) {
+    if (c->qr_nb > 0 && qr_width_fits(c->M, c->qr_nb)) return c->qr_nb;
     for (int nb = 32; nb > 8; nb >>= 1)
-        if (2 * sizeof(float2) * (size_t)M * nb <= 200 * 1024) return nb;
+        if (qr_width_fits(c->M, nb)) return nb;
     return 8;
+}
+
+cudaError_t launch_qr32(ftq_ctx* c, int nbq) {
+    const int M = c->M;
+    const size_t smq = 2 * sizeof(float2) * (size_t)M * nbq;
+    static size_t smq_set[3] = {48 * 1024, 48 * 1024, 48 * 1024};
+    const int which = nbq == 32 ? 0 : (nbq == 16 ? 1 : 2);
+    cudaError_t e;
+    if (smq > smq_set[which]) {
+        e = nbq == 32 ? cudaFuncSetAttribute(k_qr32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq)
+            : nbq == 16 ? cudaFuncSetAttribute(k_qr32<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq)
+                        : cudaFuncSetAttribute(k_qr32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+        if (e != cudaSuccess) return e;
+        smq_set[which] = smq;
+    }
+    if (nbq == 32) k_qr32<32><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
+    else if (nbq == 16) k_qr32<16><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
+    else k_qr32<8><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepiv(ftq_ctx* c, bool update_parity = true) {
+    const int M = c->M;
+    Planes P;
+    P.Kp = c->Kp;
+    P.part = (size_t)c->LD * 2 * c->Kp;
+    const size_t sm0 = (sizeof(double) + sizeof(int) + 1) * M + sizeof(float2) * 32 * 33 + 16;
+    static size_t sm0_set = 48 * 1024;
+    if (sm0 > sm0_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_prepiv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
+        if (e != cudaSuccess) return e;
+        sm0_set = sm0;
+    }
+    k_prepiv32<<<c->W, 256, sm0, c->stream>>>(c->Ypl, c->w32, c->DR, c->hh, c->perm, c->wstate, c->status, M, P,
+                                              2 * P.part, update_parity ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Time the FP32 QR for every panel width that fits (on the walkers' current
+// chain, re-pivoted before each trial; the T^-1 update is not run, so the
+// state is unchanged) and keep the fastest.
+cudaError_t qr_autotune(ftq_ctx* c, int* best_nb, float* best_ms) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t e = cudaSuccess;
+    int best = 0;
+    float bms = 1e30f;
+    for (int nb = 32; nb >= 8; nb >>= 1) {
+        if (!qr_width_fits(c->M, nb)) continue;
+        e = launch_prepiv(c, false);
+        if (e == cudaSuccess) e = launch_qr32(c, nb);     // warm-up
+        if (e == cudaSuccess) e = launch_prepiv(c, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = launch_qr32(c, nb);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < bms) { bms = ms; best = nb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    c->qr_nb = best;
+    *best_nb = best;
+    *best_ms = bms;
+    return cudaSuccess;
 }
 
 cudaError_t launch_qr_prepiv(ftq_ctx* c) {
@@ -486,34 +560,9 @@ cudaError_t launch_qr_prepiv(ftq_ctx* c) {
     cudaError_t e;
     {
         LaunchScope ls(c, FTQ_K_QRCP);
-        const size_t sm0 = (sizeof(double) + sizeof(int) + 1) * M + sizeof(float2) * 32 * 33 + 16;
-        static size_t sm0_set = 48 * 1024;
-        if (sm0 > sm0_set) {
-            e = cudaFuncSetAttribute(k_prepiv32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
-            if (e != cudaSuccess) return e;
-            sm0_set = sm0;
-        }
-        k_prepiv32<<<c->W, 256, sm0, c->stream>>>(c->Ypl, c->w32, c->DR, c->hh, c->perm, c->wstate, c->status, M,
-                                                  P, ws);
-        e = cudaGetLastError();
+        e = launch_prepiv(c);
         if (e != cudaSuccess) return e;
-        // FP32 Householder QR: the widest panel (32, 16 or 8 columns) whose two
-        // M x NB shared arrays fit
-        const int nbq = qr_panel_width(M);
-        const size_t smq = 2 * sizeof(float2) * (size_t)M * nbq;
-        static size_t smq_set[3] = {48 * 1024, 48 * 1024, 48 * 1024};
-        const int which = nbq == 32 ? 0 : (nbq == 16 ? 1 : 2);
-        if (smq > smq_set[which]) {
-            e = nbq == 32 ? cudaFuncSetAttribute(k_qr32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq)
-                : nbq == 16 ? cudaFuncSetAttribute(k_qr32<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq)
-                            : cudaFuncSetAttribute(k_qr32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
-            if (e != cudaSuccess) return e;
-            smq_set[which] = smq;
-        }
-        if (nbq == 32) k_qr32<32><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
-        else if (nbq == 16) k_qr32<16><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
-        else k_qr32<8><<<c->W, 256, smq, c->stream>>>(c->w32, c->w2_32, c->htau, c->status, M);
-        e = cudaGetLastError();
+        e = launch_qr32(c, qr_panel_width(c));
         if (e != cudaSuccess) return e;
     }
     {

@@ -84,7 +84,8 @@ def test_mixed_vs_oracle_config1(ftq, prec):
         assert np.abs(G10[w] - ref10[w].G).max() < 1e-5
         assert (ws[w, 2] > 0.5) == ref[w].alive
         if ref[w].alive:
-            assert abs(ws[w, 0] - ref[w].logw.real) < 1e-5 * max(1, abs(ref[w].logw.real))
+            # ln|w| telescopes to 2 ln det: twice the 1e-5 relative bound of the FP32 ln det
+            assert abs(ws[w, 0] - ref[w].logw.real) < 2e-5 * max(1, abs(ref[w].logdet.real))
     print(f"mixed vs oracle, M=7: max rel err G(beta) {max(errs):.2e}")
     assert max(errs) < 1e-4
 

@@ -97,7 +97,8 @@ def test_mixed_matches_fp64(ftq):
     alive = (wa[:, 2] > 0.5) & (wb[:, 2] > 0.5)
     assert alive.sum() >= W // 2
     assert np.abs(Ga[alive] - Gb[alive]).max() < 1e-5 * np.abs(Ga).max()
-    assert np.max(np.abs(wa[alive, 0] - wb[alive, 0])) < 1e-5 * max(1.0, np.max(np.abs(wa[alive, 0])))
+    # ln|w| telescopes to 2 ln det: twice the 1e-5 relative bound of the FP32 ln det
+    assert np.max(np.abs(wa[alive, 0] - wb[alive, 0])) < 2e-5 * max(1.0, np.max(np.abs(wa[alive, 3])))
     assert np.max(np.abs(ea[alive, 3] - eb[alive, 3])) < 1e-5 * np.max(np.abs(ea[alive, 3]))
 
 
