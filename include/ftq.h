@@ -43,10 +43,15 @@ extern "C" {
 /* precision of the slice chain */
 #define FTQ_FP64   0      /* every step in complex128                                   */
 #define FTQ_MIXED  1      /* B chain in 3xTF32 tensor-core math (tcgen05, FP32 accumulate),
-                             FP32 per-slice G and LU, FP64 log-determinant accumulation,
-                             complex128 QR/UDT, G(beta) and log-weights                  */
+                             FP32 per-slice G and LU, FP64 log-determinant accumulation;
+                             stabilisation: FP32 Householder of the pre-pivoted chain,
+                             D_R in FP64 and the T^-1 update in double-FP32 (48-bit)
+                             arithmetic on the FP32 pipe; complex128 G(beta),
+                             estimators and log-weights                                  */
 #define FTQ_MIXED_SIMT 2  /* as FTQ_MIXED with the chain on FP32 CUDA cores (measured
                              variant and cross-check of the tensor-core chain)          */
+#define FTQ_MIXED_F64UDT 3 /* as FTQ_MIXED with the T^-1 update on the FP64 pipe
+                             (measured variant and cross-check of the double-FP32 one)  */
 
 /* weight update */
 #define FTQ_PHASELESS 0   /* w <- |I_k| max(0, cos theta_k)  (Eqs. import, phimport, theta) */
@@ -69,7 +74,7 @@ typedef struct {
     int      walkers;          /* W > 0                                                  */
     int      stabilise_every;  /* s: QRCP of the right block every s slices (0 = never)   */
     int      exp_order;        /* p >= 1: Taylor order of exp(V)                          */
-    int      precision;        /* FTQ_FP64, FTQ_MIXED or FTQ_MIXED_SIMT                   */
+    int      precision;        /* FTQ_FP64, FTQ_MIXED, FTQ_MIXED_SIMT or FTQ_MIXED_F64UDT */
     int      constraint;       /* FTQ_PHASELESS or FTQ_FREE                               */
     int      overlap;          /* FTQ_OVERLAP_PAPER or FTQ_OVERLAP_MODIFIED               */
     uint64_t seed;             /* key of the on-device field generator (ftq_fields)       */

@@ -8,7 +8,7 @@ import ctypes
 import math
 import os
 
-FTQ_FP64, FTQ_MIXED, FTQ_MIXED_SIMT = 0, 1, 2
+FTQ_FP64, FTQ_MIXED, FTQ_MIXED_SIMT, FTQ_MIXED_F64UDT = 0, 1, 2, 3
 FTQ_PHASELESS, FTQ_FREE = 0, 1
 FTQ_OVERLAP_PAPER, FTQ_OVERLAP_MODIFIED = 0, 1
 _Q = dict(M=0, N_ALPHA=1, N_SLICES=2, SLICE=3, WALKERS=4, NCUT2=5, PRECISION=6, DEVICE_BYTES=7, QR_PANEL=8)

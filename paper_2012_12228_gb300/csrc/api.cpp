@@ -83,7 +83,8 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     if (opts->walkers <= 0) return fail(nullptr, FTQ_EINVAL, "walkers must be positive");
     if (opts->exp_order < 1 || opts->exp_order > 32) return fail(nullptr, FTQ_EINVAL, "exp_order must be in 1..32");
     if (opts->stabilise_every < 0) return fail(nullptr, FTQ_EINVAL, "stabilise_every must be >= 0");
-    if (opts->precision != FTQ_FP64 && opts->precision != FTQ_MIXED && opts->precision != FTQ_MIXED_SIMT)
+    if (opts->precision != FTQ_FP64 && opts->precision != FTQ_MIXED && opts->precision != FTQ_MIXED_SIMT &&
+        opts->precision != FTQ_MIXED_F64UDT)
         return fail(nullptr, FTQ_EINVAL, "unknown precision");
     if (opts->constraint != FTQ_PHASELESS && opts->constraint != FTQ_FREE)
         return fail(nullptr, FTQ_EINVAL, "unknown constraint");
@@ -186,7 +187,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         c->tab.neplus = (int)eplus.size();
         chk(upload(c, &c->tab.eplus, eplus));
     }
-    if (e == cudaSuccess && opts->precision == FTQ_MIXED) {
+    if (e == cudaSuccess && (opts->precision == FTQ_MIXED || opts->precision == FTQ_MIXED_F64UDT)) {
         if (!ftq::tc_supported(M)) {
             free_all(c);
             delete c;

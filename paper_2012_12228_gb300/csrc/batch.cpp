@@ -161,7 +161,7 @@ int ftq_autotune(ftq_ctx* c, int* choice, float* ms) {
     std::vector<ftq_ctx*> targets = c->members.empty() ? std::vector<ftq_ctx*>{c} : c->members;
     for (size_t s = 0; s < targets.size(); ++s) {
         ftq_ctx* m = targets[s];
-        if (m->opts.precision != FTQ_MIXED) {
+        if (m->opts.precision != FTQ_MIXED && m->opts.precision != FTQ_MIXED_F64UDT) {
             if (choice) choice[s] = 0;
             if (ms) ms[s] = 0.f;
             continue;

@@ -368,7 +368,7 @@ cudaError_t mixed_init(ftq_ctx* c) {
 
 cudaError_t mixed_chain(ftq_ctx* c) {
     const int M = c->M, p = c->opts.exp_order;
-    const bool tensor = c->opts.precision == FTQ_MIXED;
+    const bool tensor = c->opts.precision == FTQ_MIXED || c->opts.precision == FTQ_MIXED_F64UDT;
     const int tiles = (M + ST - 1) / ST;
     dim3 grid(tiles * tiles, c->W);
     const Planes P = planes_of(c);

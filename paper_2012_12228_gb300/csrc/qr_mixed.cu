@@ -403,6 +403,179 @@ __global__ void __launch_bounds__(288, 4) k_tinv64(const float2* __restrict__ A,
         for (int j = 0; j < M; ++j) Ti[(long)i * M + j] = XT[(long)j * M + i];
 }
 
+// ---------------------------------------------------------------- S3 in double-FP32
+// The same update, T^-1 <- T^-1 Pi U^-1 (X U = Z, Z = T^-1 Pi), with every
+// value carried as an unevaluated sum of two floats (hi + lo, 48 significand
+// bits) on the FP32 pipe, whose rate on this part is 64 times that of the
+// FP64 pipe.  Products are split exactly with FMA (Dekker / Knuth two-product,
+// two-sum; the lo * lo term, 2^-48 relative, is dropped) and the running sums
+// carry their rounding errors in the lo part.
+//
+// k_udt_prep (one block per walker): D_R = diag(R_Y) D', U_mj =
+//   (R_Y[m][j] / R_Y[m][m]) (D'_j / D'_m) formed in FP64 and stored as
+//   double-FP32 (Re hi, Re lo, Im hi, Im lo) in the upper triangle.
+// k_tinv_df (a block per walker and row range, one row of X per thread): the
+//   forward solve in NBJ-column blocks, the block's strip of U staged in
+//   shared memory and read at the same address by every thread; X column-major
+//   in double-FP32 in the scratch; T^-1 rows written back in FP64 through a
+//   shared tile.
+struct df2 { float h, l; };
+
+__device__ __forceinline__ df2 df_split(double v) {
+    df2 r;
+    r.h = (float)v;
+    r.l = (float)(v - (double)r.h);
+    return r;
+}
+
+// acc -= x * u  (x, u double-FP32; acc.l collects the rounding errors)
+__device__ __forceinline__ void df_msub(df2& acc, float xh, float xl, float uh, float ul) {
+    const float p = xh * uh;
+    float e = fmaf(xh, uh, -p);
+    e = fmaf(xh, ul, e);
+    e = fmaf(xl, uh, e);
+    const float t = acc.h - p;
+    const float bb = t - acc.h;
+    const float err = (acc.h - (t - bb)) + (-p - bb);
+    acc.h = t;
+    acc.l += err - e;
+}
+
+// acc += x * u
+__device__ __forceinline__ void df_madd(df2& acc, float xh, float xl, float uh, float ul) {
+    df_msub(acc, -xh, -xl, uh, ul);
+}
+
+__device__ __forceinline__ df2 df_norm(df2 a) {
+    df2 r;
+    r.h = a.h + a.l;
+    r.l = a.l - (r.h - a.h);
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_udt_prep(const float2* __restrict__ A, const double2* __restrict__ Dp,
+                                                 float4* __restrict__ Udf, double2* __restrict__ DR,
+                                                 int* __restrict__ status, int M) {
+    extern __shared__ unsigned char smem_raw[];
+    double2* dinv = reinterpret_cast<double2*>(smem_raw);   // [M] 1 / (R_Y[m][m] D'_m)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int w = blockIdx.x;
+    const long off = (long)w * M * M;
+    const float2* Aw = A + off;
+    const double2* Dpw = Dp + (long)w * M;
+    for (int j = tid; j < M; j += nt) {
+        const float2 r = Aw[(long)j * M + j];
+        const double2 d = cmul(make_double2(r.x, r.y), Dpw[j]);
+        DR[(long)w * M + j] = d;
+        if (!(abs2(d) > 0.0)) atomicOr(status, 1);
+        dinv[j] = cinv(d);
+    }
+    __syncthreads();
+    float4* U = Udf + off;
+    for (long e = tid; e < (long)M * M; e += nt) {
+        const int m = (int)(e / M), j = (int)(e % M);
+        if (j > m) {
+            const float2 r = Aw[e];
+            const double2 u = cmul(cmul(make_double2(r.x, r.y), Dpw[j]), dinv[m]);
+            const df2 re = df_split(u.x), im = df_split(u.y);
+            U[e] = make_float4(re.h, re.l, im.h, im.l);
+        }
+    }
+}
+
+template <int NBJ>
+__global__ void __launch_bounds__(128) k_tinv_df(const float4* __restrict__ Udf, const int* __restrict__ permg,
+                                                 float4* __restrict__ Xs, double2* __restrict__ Tinv,
+                                                 int* __restrict__ status, int M) {
+    extern __shared__ unsigned char smem_raw[];
+    const int RB = blockDim.x;
+    // the strip of U ([M][NBJ] float4) and, at the end, the output tile
+    // ([16][RB + 1] double2, 16 bytes each as well) share the first region
+    const size_t sreg = max((size_t)M * NBJ, (size_t)16 * (RB + 1));
+    float4* S = reinterpret_cast<float4*>(smem_raw);
+    int* perm = reinterpret_cast<int*>(S + sreg);           // [M]
+    const int tid = threadIdx.x, w = blockIdx.y;
+    const int i = blockIdx.x * RB + tid;
+    const bool row = i < M;
+    const long off = (long)w * M * M;
+    const float4* U = Udf + off;
+    float4* X = Xs + off;
+    double2* Ti = Tinv + off;
+    for (int m = tid; m < M; m += RB) perm[m] = permg[(long)w * M + m];
+    bool bad = false;
+    for (int jb = 0; jb < M; jb += NBJ) {
+        const int nb = min(NBJ, M - jb);
+        __syncthreads();
+        for (int e = tid; e < (jb + nb) * NBJ; e += RB) {   // columns q >= nb and the lower part zero
+            const int m = e / NBJ, q = e % NBJ;
+            S[e] = (q < nb && m < jb + q) ? U[(long)m * M + jb + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        if (!row) continue;
+        df2 sr[NBJ], si[NBJ];
+#pragma unroll
+        for (int q = 0; q < NBJ; ++q) {
+            const double2 z = q < nb ? Ti[(long)i * M + perm[jb + q]] : make_double2(0.0, 0.0);
+            sr[q] = df_split(z.x);
+            si[q] = df_split(z.y);
+        }
+        for (int m = 0; m < jb; ++m) {
+            const float4 x = X[(long)m * M + i];
+            const float4* ur = S + m * NBJ;
+#pragma unroll
+            for (int q = 0; q < NBJ; ++q) {
+                const float4 u = ur[q];
+                // s -= x u: Re -= xr ur - xi ui, Im -= xr ui + xi ur
+                df_msub(sr[q], x.x, x.y, u.x, u.y);
+                df_madd(sr[q], x.z, x.w, u.z, u.w);
+                df_msub(si[q], x.x, x.y, u.z, u.w);
+                df_msub(si[q], x.z, x.w, u.x, u.y);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NBJ; ++q) {
+            if (q >= nb) continue;
+#pragma unroll
+            for (int q2 = 0; q2 < NBJ; ++q2) {
+                if (q2 >= q) continue;
+                const float4 u = S[(jb + q2) * NBJ + q];
+                const df2 xr = sr[q2], xi = si[q2];
+                df_msub(sr[q], xr.h, xr.l, u.x, u.y);
+                df_madd(sr[q], xi.h, xi.l, u.z, u.w);
+                df_msub(si[q], xr.h, xr.l, u.z, u.w);
+                df_msub(si[q], xi.h, xi.l, u.x, u.y);
+            }
+            sr[q] = df_norm(sr[q]);
+            si[q] = df_norm(si[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NBJ; ++q)
+            if (q < nb) {
+                X[(long)(jb + q) * M + i] = make_float4(sr[q].h, sr[q].l, si[q].h, si[q].l);
+                bad = bad || !isfinite(sr[q].h) || !isfinite(si[q].h);
+            }
+    }
+    if (bad) atomicOr(status, 1);
+    // T^-1 rows of this block in FP64 (hi + lo), 16 columns at a time through the tile
+    double2* tile = reinterpret_cast<double2*>(S);
+    const int r0 = blockIdx.x * RB;
+    const int nrow = min(RB, M - r0);
+    for (int cb = 0; cb < M; cb += 16) {
+        __syncthreads();
+        if (row)
+            for (int cc = 0; cc < 16; ++cc)
+                if (cb + cc < M) {
+                    const float4 x = X[(long)(cb + cc) * M + i];
+                    tile[cc * (RB + 1) + tid] = make_double2((double)x.x + (double)x.y, (double)x.z + (double)x.w);
+                }
+        __syncthreads();
+        for (int e = tid; e < nrow * 16; e += RB) {
+            const int r = e >> 4, cc = e & 15;
+            if (cb + cc < M) Ti[(long)(r0 + r) * M + cb + cc] = tile[cc * (RB + 1) + r];
+        }
+    }
+}
+
 // Q[:, c0 .. c0+32) = H_0 ... H_{M-1} e_c, accumulated backwards in shared
 // memory (reflector j only touches rows >= j and columns >= j).
 __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT, const double* __restrict__ htau,
@@ -551,6 +724,41 @@ cudaError_t qr_autotune(ftq_ctx* c, int* best_nb, float* best_ms) {
     return cudaSuccess;
 }
 
+constexpr int TNBJ = 8;   // columns per block of the double-FP32 solve
+
+size_t tinv_df_smem(int M, int RB) {
+    const size_t sreg = (size_t)M * TNBJ > (size_t)16 * (RB + 1) ? (size_t)M * TNBJ : (size_t)16 * (RB + 1);
+    return sizeof(float4) * sreg + sizeof(int) * M;
+}
+
+cudaError_t launch_tinv_df(ftq_ctx* c) {
+    const int M = c->M;
+    float4* U = reinterpret_cast<float4*>(c->work);       // double-FP32 U, [W][M][M] (16 bytes per entry)
+    float4* X = reinterpret_cast<float4*>(c->work2);      // double-FP32 X, column-major
+    const size_t sm0 = sizeof(double2) * M;
+    static size_t sm0_set = 48 * 1024;
+    cudaError_t e;
+    if (sm0 > sm0_set) {
+        e = cudaFuncSetAttribute(k_udt_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0);
+        if (e != cudaSuccess) return e;
+        sm0_set = sm0;
+    }
+    k_udt_prep<<<c->W, 256, sm0, c->stream>>>(c->w32, c->hh, U, c->DR, c->status, M);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nblk = (M + 127) / 128;
+    const int RB = ((M + nblk - 1) / nblk + 31) / 32 * 32;     // rows per block, <= 128
+    const size_t sm = tinv_df_smem(M, RB);
+    static size_t sm_set = 48 * 1024;
+    if (sm > sm_set) {
+        e = cudaFuncSetAttribute(k_tinv_df<TNBJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        sm_set = sm;
+    }
+    k_tinv_df<TNBJ><<<dim3((unsigned)nblk, (unsigned)c->W), RB, sm, c->stream>>>(U, c->perm, X, c->Tinv, c->status, M);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_qr_prepiv(ftq_ctx* c) {
     const int M = c->M;
     Planes P;
@@ -565,7 +773,11 @@ cudaError_t launch_qr_prepiv(ftq_ctx* c) {
         e = launch_qr32(c, qr_panel_width(c));
         if (e != cudaSuccess) return e;
     }
-    {
+    if (c->opts.precision != FTQ_MIXED_F64UDT) {
+        LaunchScope ls(c, FTQ_K_TINV);
+        e = launch_tinv_df(c);
+        if (e != cudaSuccess) return e;
+    } else {
         LaunchScope ls(c, FTQ_K_TINV);
         int nt = (M + 31) / 32 * 32;
         nt = nt < 64 ? 64 : (nt > 288 ? 288 : nt);          // the launch bound; every loop strides by nt
