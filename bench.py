@@ -547,6 +547,8 @@ def measure_lowrank(ftq, torch, dev, W, thr=1e-6):
         p.close()
     res["compression"] = [compression_trace(ftq, torch, dev, stream, t_, thr)
                           for t_ in (0.125, 0.5)]
+    res["compression_m1189"] = [compression_trace(ftq, torch, dev, stream, t_, thr, W=8, M=1189)
+                                for t_ in (0.125, 0.5)]
     res.update({"workload": "ueg_n14_m515 (r_s=0.5, Theta=0.125, dtau=0.05)", "M": c["M"], "walkers": W,
                 "n_slices": n, "precision": "c128",
                 "speedup": res["low_rank"]["value"] / res["full_rank"]["value"],
@@ -555,13 +557,15 @@ def measure_lowrank(ftq, torch, dev, W, thr=1e-6):
     return res
 
 
-def compression_trace(ftq, torch, dev, stream, theta, thr, W=16, dtau=0.01):
-    """Ranks along the path of N = 14, M = 515, r_s = 0.5 at temperature
-    Theta (dtau = 0.01): m_R (largest over the walkers) after every
-    stabilisation, m_L of the trial block and m_T = min(m_R, m_L) at the same
-    slices, and the compression 1 - m/M of each (the quantities of the
-    paper's low-rank compression figure)."""
-    c = LOWRANK
+def compression_trace(ftq, torch, dev, stream, theta, thr, W=16, dtau=0.01, M=None):
+    """Ranks along the path of N = 14, M = 515 (or the given M), r_s = 0.5 at
+    temperature Theta (dtau = 0.01): m_R (largest over the walkers) after
+    every stabilisation, m_L of the trial block and m_T = min(m_R, m_L) at
+    the same slices, and the compression 1 - m/M of each (the quantities of
+    the paper's low-rank compression figure, whose basis is M = 1189)."""
+    c = dict(LOWRANK)
+    if M is not None:
+        c["M"] = M
     p = ftq.Propagator(c["N"], c["M"], c["rs"], theta, dtau, walkers=W, stabilise_every=5, exp_order=6,
                        precision=ftq.FTQ_FP64, stream=stream, low_rank=thr)
     n, na, M = p.n_slices, p.n_alpha, p.M
@@ -577,7 +581,7 @@ def compression_trace(ftq, torch, dev, stream, theta, thr, W=16, dtau=0.01):
         rows.append({"tau": k * dt, "m_R": m_r, "m_L": m_l, "m_T": min(m_r, m_l)})
     status = p.status()
     p.close()
-    return {"theta": theta, "dtau": dt, "n_slices": n, "walkers": W, "status": status, "trace": rows,
+    return {"M": M, "theta": theta, "dtau": dt, "n_slices": n, "walkers": W, "status": status, "trace": rows,
             "mean_compression_T": float(np.mean([1.0 - r["m_T"] / M for r in rows]))}
 
 
@@ -686,7 +690,8 @@ def run_ours(args, rank, world, local_rank):
         ragged = measure_ragged(ftq, torch, dev)
     others = None
     if args.precision == "mixed" and not args.no_configs and rank == 0:
-        others = {"ueg_n14_m57": {p_: measure_config(ftq, torch, dev, "ueg_n14_m57", p_) for p_ in ("mixed", "fp64")},
+        others = {"ueg_n2_m7": measure_config(ftq, torch, dev, "ueg_n2_m7", "fp64"),
+                  "ueg_n14_m57": {p_: measure_config(ftq, torch, dev, "ueg_n14_m57", p_) for p_ in ("mixed", "fp64")},
                   "ueg_n14_m123": measure_config(ftq, torch, dev, "ueg_n14_m123", "fp64", with_mu=True)}
     if rank != 0:
         return

@@ -102,7 +102,8 @@ typedef struct {
 
 /* Create a UEG system and W walkers at tau = 0 (A(0) = B_T^n).
  *   N      target electron number N-bar (even, 0 < N < 2M)
- *   M      plane-wave basis size; must be a closed-shell count (7, 19, 27, 33, 57, ...)
+ *   M      plane-wave basis size; must be a closed-shell count (7, 19, 27, 33, 57, ...),
+ *          at most 2047 with FTQ_FP64 and 1021 with the mixed precisions
  *   rs     Wigner-Seitz radius;  L = (4 pi N / 3)^(1/3) rs     (Computational Details)
  *   theta  T / T_F with k_B T_F = (9 pi / 4)^(2/3) / (2 rs^2)  (Eq. fermiT)
  *   mu     chemical potential of B; NaN selects mu = mu_T      (Sec. Phaseless approximation)

@@ -19,6 +19,7 @@ int fail(ftq_ctx* c, int code, const std::string& msg) {
 }
 
 int cuda_fail(ftq_ctx* c, cudaError_t e, const char* where) {
+    cudaGetLastError();     // a non-sticky error must not be reported again by a later call
     return fail(c, FTQ_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -104,9 +105,15 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         delete c;
         return fail(nullptr, FTQ_EINVAL, why);
     }
-    if (M > 1024) {
+    // the per-walker kernels loop over rows and columns with at most 1024
+    // threads; their shared arrays grow with M (and with the number of
+    // transfers): the complex128 path is checked up to M = 1189, the mixed
+    // path up to M = 1021
+    const int max_m = opts->precision == FTQ_FP64 ? 2047 : 1021;
+    if (M > max_m) {
         delete c;
-        return fail(nullptr, FTQ_EINVAL, "M > 1024 is not supported by the per-walker factorisation kernels");
+        return fail(nullptr, FTQ_EINVAL, "M = " + std::to_string(M) + " exceeds " + std::to_string(max_m) +
+                                              " for this precision");
     }
     c->opts = *opts;
     c->stream = reinterpret_cast<cudaStream_t>(opts->cuda_stream);
@@ -200,6 +207,7 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     if (e != cudaSuccess) {
         int code = (e == cudaErrorMemoryAllocation) ? FTQ_ENOMEM : FTQ_ECUDA;
         std::string msg = std::string("device setup failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
         free_all(c);
         delete c;
         return fail(nullptr, code, msg);
@@ -265,8 +273,13 @@ int ftq_fields(ftq_ctx* c, int first_slice, int n_slices, double* out_dev) {
     return FTQ_OK;
 }
 
+// The structure factor and the mu derivative keep two tables over every
+// transfer in shared memory (32 bytes per slot).
+static bool slot_tables_fit(const ftq_ctx* c) { return 2 * sizeof(double2) * (size_t)c->nslot <= 227 * 1024; }
+
 int ftq_structure_factor(ftq_ctx* c, double* out_host, void* per_walker_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!slot_tables_fit(c)) return fail(c, FTQ_EINVAL, "too many momentum transfers for the structure factor kernel");
     CallerOrder order(c);
     if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
     if (!c->members.empty()) return fail(c, FTQ_EINVAL, "evaluate the members of a batch one by one");
@@ -368,6 +381,7 @@ int ftq_slice_estimates(ftq_ctx* c, double* out_host, int capacity) {
 
 int ftq_mu_grad(ftq_ctx* c, double* out_host, double* per_walker_dev) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (!slot_tables_fit(c)) return fail(c, FTQ_EINVAL, "too many momentum transfers for the mu-derivative kernel");
     CallerOrder order(c);
     if (!out_host) return fail(c, FTQ_EINVAL, "out_host must not be NULL");
     if (c->k != c->sys.n_slices)

@@ -577,6 +577,30 @@ void tc_plan(int M, int nct, int* R, int* NT) {
     else *NT = 256;                                     // border columns [256 nct, M) on CUDA cores
 }
 
+// Dynamic shared memory of k_chain_tc: two stages of A (hi, lo) and B
+// (hi, lo) tiles, the field table, the packed basis and the difference cube.
+size_t tc_smem_bytes(int nt_max, int nslot_max, int m_max, int qsize_max) {
+    const size_t stage = 2 * (size_t)AROWS * KTILE * 4 + 2 * (size_t)nt_max * KTILE * 4;
+    return 1024 + 2 * stage + sizeof(float2) * nslot_max + sizeof(int) * m_max + sizeof(uint16_t) * qsize_max;
+}
+
+constexpr size_t TC_SMEM_LIMIT = 227 * 1024 - 2048;   // leaves room for the kernel's static shared memory
+
+bool tc_fits(const ftq_ctx* c, int nct) {
+    int R, NT;
+    tc_plan(c->M, nct, &R, &NT);
+    const int qsize = c->sys.qS * c->sys.qS * c->sys.qS;
+    return tc_smem_bytes(NT, c->nslot, c->M, qsize) <= TC_SMEM_LIMIT;
+}
+
+// The fewest column tiles (1 .. 8) whose tile width lets the shared memory
+// fit; 0 when none does.
+int tc_min_nct(const ftq_ctx* c) {
+    for (int nct = 1; nct <= 8; ++nct)
+        if (tc_fits(c, nct)) return nct;
+    return 0;
+}
+
 bool tc_supported(int M) {
     (void)M;
     return encode_fn() != nullptr;
@@ -589,6 +613,9 @@ int tmem_cols(int NT) { return NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128
 cudaError_t tc_make_maps(ftq_ctx* c) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
+    const int nmin = tc_min_nct(c);
+    if (nmin == 0) return cudaErrorInvalidValue;
+    if (c->nct < nmin) c->nct = nmin;
     int R, NT;
     tc_plan(c->M, c->nct, &R, &NT);
     float* bufs[3] = {c->Ypl, c->zpl[0], c->zpl[1]};
@@ -653,8 +680,7 @@ bool fill_args(ftq_ctx* c, const float* zin, float* out, const double* zs, const
 }
 
 size_t tc_smem(int nt_max, int nslot_max, int m_max, int qsize_max) {
-    const size_t stage = 2 * (size_t)AROWS * KTILE * 4 + 2 * (size_t)nt_max * KTILE * 4;
-    return 1024 + 2 * stage + sizeof(float2) * nslot_max + sizeof(int) * m_max + sizeof(uint16_t) * qsize_max;
+    return tc_smem_bytes(nt_max, nslot_max, m_max, qsize_max);
 }
 
 cudaError_t launch_items(ftq_ctx* timing_ctx, const TcBatch& tb, const int4* items, int nitems, cudaStream_t st) {
@@ -775,7 +801,8 @@ cudaError_t tc_batch_items(ftq_ctx* b) {
 cudaError_t tc_autotune(ftq_ctx* c, int* best_nct, float* best_ms) {
     int best = c->nct;
     float bms = 1e30f;
-    const int cands[3] = {1, 2, 3};
+    const int n0 = tc_min_nct(c) > 0 ? tc_min_nct(c) : 1;
+    const int cands[3] = {n0, n0 + 1, n0 + 2};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -784,6 +811,7 @@ cudaError_t tc_autotune(ftq_ctx* c, int* best_nct, float* best_ms) {
         int R, NT;
         tc_plan(c->M, nct, &R, &NT);
         if (nct > 1 && NT * (nct - 1) >= c->M) continue;   // an empty column tile
+        if (!tc_fits(c, nct)) continue;
         c->nct = nct;
         e = tc_make_maps(c);
         if (e != cudaSuccess) break;

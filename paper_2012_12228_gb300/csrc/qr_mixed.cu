@@ -17,7 +17,7 @@
 //   k_qr32 (one block per walker): blocked Householder QR of A in FP32
 //       (compact WY panels of NB columns); R_Y in A, reflectors and tau out.
 //   k_tinv64 (FP64, one block per walker): D_R, U and T^-1 <- T^-1 Pi U^-1.
-//   k_form_q32 (FP32, one block per walker and 32-column panel): Q = H_0 ...
+//   k_form_q32 (FP32, one block per walker and 32- or 16-column panel): Q = H_0 ...
 //       H_{M-1} applied to the identity panel in shared memory, written into
 //       the chain planes as the new Y.
 #include <cmath>
@@ -29,7 +29,6 @@
 namespace ftq {
 namespace {
 
-constexpr int QP = 32;   // columns per Q panel
 constexpr int NBJ = 2;   // columns per block of the T^-1 update
 
 // ---------------------------------------------------------------- S1: pre-pivoting
@@ -576,18 +575,21 @@ __global__ void __launch_bounds__(128) k_tinv_df(const float4* __restrict__ Udf,
     }
 }
 
-// Q[:, c0 .. c0+32) = H_0 ... H_{M-1} e_c, accumulated backwards in shared
-// memory (reflector j only touches rows >= j and columns >= j).
+// Q[:, c0 .. c0+QP) = H_0 ... H_{M-1} e_c, accumulated backwards in shared
+// memory (reflector j only touches rows >= j and columns >= j); 256 threads
+// as QP columns x (256 / QP) row groups.
+template <int QP>
 __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT, const double* __restrict__ htau,
                                                  float* __restrict__ Ypl, float* __restrict__ Yf, int M, Planes P,
                                                  size_t wstride) {
     extern __shared__ unsigned char smem_raw[];
     float2* Qp = reinterpret_cast<float2*>(smem_raw);     // [M][QP]
     float2* ub = Qp + (size_t)M * QP;                     // [M]
-    __shared__ float2 part[8][QP];
+    constexpr int NG = 256 / QP;                          // row groups
+    __shared__ float2 part[NG][QP];
     __shared__ float2 wv[QP];
     const int tid = threadIdx.x;
-    const int cc = tid & (QP - 1), g = tid >> 5;          // column in panel, row group (8 groups)
+    const int cc = tid & (QP - 1), g = tid / QP;          // column in panel, row group
     const int w = blockIdx.y;
     const int c0 = blockIdx.x * QP;
     const int ncol = min(QP, M - c0);
@@ -605,7 +607,7 @@ __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT,
         __syncthreads();
         float2 s = make_float2(0.f, 0.f);
         if (cc < ncol && c0 + cc >= j)
-            for (int r = j + g; r < M; r += 8) {
+            for (int r = j + g; r < M; r += NG) {
                 const float2 u = ub[r], q = Qp[r * QP + cc];
                 s.x = fmaf(u.x, q.x, fmaf(u.y, q.y, s.x));     // conj(u) q
                 s.y = fmaf(u.x, q.y, fmaf(-u.y, q.x, s.y));
@@ -615,14 +617,14 @@ __global__ void __launch_bounds__(256) k_form_q32(const float2* __restrict__ VT,
         if (g == 0) {
             float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) t = t + part[k][cc];
+            for (int k = 0; k < NG; ++k) t = t + part[k][cc];
             const float tj = (float)tau[j];
             wv[cc] = make_float2(t.x * tj, t.y * tj);
         }
         __syncthreads();
         if (cc < ncol && c0 + cc >= j) {
             const float2 wc = wv[cc];
-            for (int r = j + g; r < M; r += 8) {
+            for (int r = j + g; r < M; r += NG) {
                 const float2 u = ub[r];
                 float2 q = Qp[r * QP + cc];
                 q.x = fmaf(-u.x, wc.x, fmaf(u.y, wc.y, q.x));
@@ -793,16 +795,21 @@ cudaError_t launch_qr_prepiv(ftq_ctx* c) {
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    // 32-column Q panels while they fit in shared memory, else 16
+    const bool wide = sizeof(float2) * ((size_t)M * 32 + M) <= 200 * 1024;
+    const int QP = wide ? 32 : 16;
     const size_t sm2 = sizeof(float2) * ((size_t)M * QP + M);
-    static size_t sm2_set = 48 * 1024;
-    if (sm2 > sm2_set) {
-        e = cudaFuncSetAttribute(k_form_q32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    static size_t sm2_set[2] = {48 * 1024, 48 * 1024};
+    if (sm2 > sm2_set[wide]) {
+        e = wide ? cudaFuncSetAttribute(k_form_q32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)
+                 : cudaFuncSetAttribute(k_form_q32<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
         if (e != cudaSuccess) return e;
-        sm2_set = sm2;
+        sm2_set[wide] = sm2;
     }
     LaunchScope ls(c, FTQ_K_BRIDGE);
-    k_form_q32<<<dim3((unsigned)((M + QP - 1) / QP), (unsigned)c->W), 256, sm2, c->stream>>>(c->w2_32, c->htau,
-                                                                                          c->Ypl, c->Yf, M, P, ws);
+    const dim3 grid((unsigned)((M + QP - 1) / QP), (unsigned)c->W);
+    if (wide) k_form_q32<32><<<grid, 256, sm2, c->stream>>>(c->w2_32, c->htau, c->Ypl, c->Yf, M, P, ws);
+    else k_form_q32<16><<<grid, 256, sm2, c->stream>>>(c->w2_32, c->htau, c->Ypl, c->Yf, M, P, ws);
     return cudaGetLastError();
 }
 
