@@ -512,9 +512,10 @@ def measure_lowrank(ftq, torch, dev, W, thr=1e-6):
     c = LOWRANK
     stream = torch.cuda.current_stream(dev)
     res = {}
-    for t in (0.0, thr):
+    for t, prec, name in ((0.0, ftq.FTQ_FP64, "full_rank"), (thr, ftq.FTQ_FP64, "low_rank"),
+                          (0.0, ftq.FTQ_MIXED, "mixed_full_rank"), (thr, ftq.FTQ_MIXED, "mixed_low_rank")):
         p = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, stabilise_every=5,
-                           exp_order=6, precision=ftq.FTQ_FP64, stream=stream, low_rank=t)
+                           exp_order=6, precision=prec, stream=stream, low_rank=t)
         n, na = p.n_slices, p.n_alpha
         f = torch.from_numpy(gaussian_fields(c["seed"], n, W, na)).to(dev)
         p.propagate(f[:1].contiguous())          # warm-up (first launches, shared-memory attributes)
@@ -532,7 +533,7 @@ def measure_lowrank(ftq, torch, dev, W, thr=1e-6):
         out = {"value": W * n / (ms / 1e3), "unit": "walker-slices/s", "ms_path": ms,
                "E_per_electron": float(np.mean(pw[alive, 3]) / c["N"]), "N": float(np.mean(pw[alive, 5])),
                "alive": int(alive.sum()), "status": p.status()}
-        if t > 0:
+        if t > 0 and prec == ftq.FTQ_FP64:
             trace = []
             p.reset()
             for k0 in range(0, n, 5):
@@ -543,15 +544,19 @@ def measure_lowrank(ftq, torch, dev, W, thr=1e-6):
             m_left = [int(np.sum(np.exp(-(n - k) * dt * (eps - mu_t)) >= t)) for k in range(5, n + 1, 5)]
             out.update({"threshold": t, "m_R_max_after_each_stabilisation": trace,
                         "m_L_at_each_stabilisation": m_left})
-        res["low_rank" if t > 0 else "full_rank"] = out
+        res[name] = out
         p.close()
     res["compression"] = [compression_trace(ftq, torch, dev, stream, t_, thr)
                           for t_ in (0.125, 0.5)]
     res["compression_m1189"] = [compression_trace(ftq, torch, dev, stream, t_, thr, W=8, M=1189)
                                 for t_ in (0.125, 0.5)]
     res.update({"workload": "ueg_n14_m515 (r_s=0.5, Theta=0.125, dtau=0.05)", "M": c["M"], "walkers": W,
-                "n_slices": n, "precision": "c128",
+                "n_slices": n, "precision": "c128 and mixed (tensor-core chain on the kept columns)",
                 "speedup": res["low_rank"]["value"] / res["full_rank"]["value"],
+                "mixed_speedup": res["mixed_low_rank"]["value"] / res["mixed_full_rank"]["value"],
+                "mixed_low_rank_over_fp64_low_rank": res["mixed_low_rank"]["value"] / res["low_rank"]["value"],
+                "mixed_low_rank_E_per_electron_abs_diff": abs(res["mixed_low_rank"]["E_per_electron"]
+                                                              - res["low_rank"]["E_per_electron"]),
                 "E_per_electron_abs_diff": abs(res["low_rank"]["E_per_electron"] - res["full_rank"]["E_per_electron"]),
                 "N_abs_diff": abs(res["low_rank"]["N"] - res["full_rank"]["N"])})
     return res

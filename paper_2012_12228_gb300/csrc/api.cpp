@@ -45,7 +45,7 @@ void free_all(ftq_ctx* c) {
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
                     c->tab.hf, c->phi32, c->xbuf, c->xsum, c->pc_w, c->pc_cnt, c->pc_parent, c->pc_pairs,
-                    c->sq_walker, c->sq_w, c->sq_out, c->Yf, c->tab.eplus, c->trk, c->trk_out};
+                    c->sq_walker, c->sq_w, c->sq_out, c->Yf, c->tab.eplus, c->trk, c->trk_out, c->items_lr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -95,8 +95,8 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         return fail(nullptr, FTQ_EINVAL, "force_bias_cap must be 0: no force-bias cap is implemented");
     if (!(opts->low_rank_threshold >= 0.0) || !std::isfinite(opts->low_rank_threshold))
         return fail(nullptr, FTQ_EINVAL, "low_rank_threshold must be finite and >= 0");
-    if (opts->low_rank_threshold > 0.0 && opts->precision != FTQ_FP64)
-        return fail(nullptr, FTQ_EINVAL, "low-rank truncation runs on the complex128 path (FTQ_FP64)");
+    if (opts->low_rank_threshold > 0.0 && opts->precision == FTQ_MIXED_SIMT)
+        return fail(nullptr, FTQ_EINVAL, "low-rank truncation runs with FTQ_FP64 or the tensor-core mixed path");
     if (N % 2 != 0) return fail(nullptr, FTQ_EINVAL, "N must be even (unpolarised gas)");
     ftq_ctx* c = new (std::nothrow) ftq_ctx();
     if (!c) return fail(nullptr, FTQ_ENOMEM, "host allocation failed");
@@ -123,9 +123,10 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
     const size_t W = c->W, MM = (size_t)M * M;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    if (opts->precision == FTQ_FP64) {
-        chk(dalloc(c, &c->Y, W * MM));
-    } else {
+    if (opts->precision == FTQ_FP64 || opts->low_rank_threshold > 0.0) {
+        chk(dalloc(c, &c->Y, W * MM));      // the mixed low-rank path keeps a complex128 copy of the chain
+    }
+    if (opts->precision != FTQ_FP64) {
         c->Kp = (M + 15) / 16 * 16;       // 2 Kp is a whole number of 32-float k tiles
         c->LD = (M + 7) / 8 * 8;
         const size_t wsz = 2 * (size_t)c->LD * 2 * c->Kp;
@@ -220,6 +221,10 @@ int ftq_reset(ftq_ctx* c) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
     c->resampled = false;
     c->trk_n = 0;
+    if (c->items_lr) {                 // every walker is back at full rank
+        cudaFree(c->items_lr);
+        c->items_lr = nullptr;
+    }
     cudaError_t e = ftq::launch_init_walkers(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "reset");
     return FTQ_OK;
@@ -302,6 +307,8 @@ int ftq_pair_branch(ftq_ctx* c, const double* draws_host, int* parent_dev) {
     for (int k = 0; k < c->W / 2; ++k)
         if (!(draws_host[k] >= 0.0 && draws_host[k] < 1.0)) return fail(c, FTQ_EINVAL, "draws must lie in [0, 1)");
     cudaError_t e = ftq::launch_pair_branch(c, draws_host, parent_dev);
+    // copied walkers carry their ranks: the rank-compacted chain work list follows
+    if (e == cudaSuccess && c->items_lr) e = ftq::tc_items_by_rank(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "pair branching");
     c->resampled = true;
     return FTQ_OK;
@@ -315,6 +322,7 @@ int ftq_population_control(ftq_ctx* c, double xi, int* parent_dev) {
     if (c->opts.constraint == FTQ_FREE) return fail(c, FTQ_EINVAL, "the comb acts on phaseless weights");
     if (c->W > 65535) return fail(c, FTQ_EINVAL, "at most 65535 walkers");
     cudaError_t e = ftq::launch_population_control(c, xi, parent_dev);
+    if (e == cudaSuccess && c->items_lr) e = ftq::tc_items_by_rank(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "population control");
     c->resampled = true;
     return FTQ_OK;

@@ -70,6 +70,8 @@ int ftq_init_batch(ftq_ctx** out, int nsys, const ftq_system* systems, const ftq
     if (nsys < 1 || nsys > 8) return bfail(nullptr, FTQ_EINVAL, "a batch holds 1 to 8 systems");
     if (opts->precision != FTQ_MIXED)
         return bfail(nullptr, FTQ_EINVAL, "a ragged batch runs the mixed-precision tensor-core path (FTQ_MIXED)");
+    if (opts->low_rank_threshold != 0.0)
+        return bfail(nullptr, FTQ_EINVAL, "a ragged batch runs at full rank");
     ftq_ctx* b = new ftq_ctx();
     b->opts = *opts;
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);

@@ -188,7 +188,9 @@ struct TcBatch {
 //       to tfull[buffer]); once the previous MMA group has drained it
 //       prefetches the next B tile into the freed stage.
 // Stage counters run over all k tiles of all items a CTA processes, buffer
-// counters over its items, so mbarrier phases stay consistent.  Every wait is
+// counters over its items, so mbarrier phases stay consistent.  An item with
+// system index -1 ends the list (work lists compacted by the walkers' ranks
+// keep their active items first); every role stops there.  Every wait is
 // bounded; on expiry the kernel latches bit 2 of the status word, every role
 // skips its remaining work (all warps still pass the same barriers), the
 // control thread drains its own copies and MMAs, and TMEM is freed.
@@ -271,9 +273,9 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                 last_tma = gi;
             };
             bool ok = true;
-            if ((int)blockIdx.x < nitems) issue_tma(items[blockIdx.x], 0, 0);
+            if ((int)blockIdx.x < nitems && items[blockIdx.x].x >= 0) issue_tma(items[blockIdx.x], 0, 0);
             int li = 0;                                   // items of this CTA so far
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+            for (int item = blockIdx.x; item < nitems && ok && items[item].x >= 0; item += gridDim.x, ++li) {
                 const int4 it = items[item];
                 const int4 nx = item + (int)gridDim.x < nitems ? items[item + gridDim.x] : make_int4(0, 0, 0, 0);
                 const TcArgs& p = tb.args[it.x];
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                     if (g >= 1) ok = mbar_wait_ab(&mma_bar[s ^ 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st, tb.wait_limit);
                     if (!ok) break;
                     if (kt + 1 < p.ktiles) issue_tma(it, kt + 1, g + 1);
-                    else if (item + (int)gridDim.x < nitems) issue_tma(nx, 0, g + 1);
+                    else if (item + (int)gridDim.x < nitems && nx.x >= 0) issue_tma(nx, 0, g + 1);
                 }
             }
             if (!ok) {   // abort latched: drain this CTA's own copies and MMAs
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
         int loaded_sys = -1;
         // swizzled offsets: row j = gw + 8 t has (j & 7) = gw and (j >> 3) = t
         const uint32_t off_top = (uint32_t)(gw * 128 + ((((lane >> 2) ^ gw) & 7) << 4) + (lane & 3) * 4);
-        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        for (int item = blockIdx.x; item < nitems && items[item].x >= 0; item += gridDim.x) {
             const int4 it = items[item];
             const TcArgs& p = tb.args[it.x];
             const int w = it.y, rows0 = it.z * 64;
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
     } else {
         // ------------------------------------------------ epilogue warps
         int li = 0;
-        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
+        for (int item = blockIdx.x; item < nitems && items[item].x >= 0; item += gridDim.x, ++li) {
             const int4 it = items[item];
             const TcArgs& p = tb.args[it.x];
             const int tb_i = li & 1;
@@ -637,6 +639,8 @@ cudaError_t tc_make_maps(ftq_ctx* c) {
             for (int ct = 0; ct < c->nct; ++ct) items.push_back(make_int4(0, w, rb, ct));
     if (c->items) cudaFree(c->items);
     c->items = nullptr;
+    if (c->items_lr) cudaFree(c->items_lr);      // rebuilt from the ranks at the next stabilisation
+    c->items_lr = nullptr;
     cudaError_t e = cudaMalloc(&c->items, sizeof(int4) * items.size());
     if (e != cudaSuccess) return e;
     c->nitems = (int)items.size();
@@ -741,7 +745,8 @@ cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double
     tb.qsize_max = tb.args[0].qsize;
     tb.ncols = tmem_cols(NT);
     tb.wait_limit = c->wait_limit >= 0 ? (long long)c->wait_limit : (long long)WAIT_LIMIT;
-    cudaError_t e = launch_items(c, tb, c->items, c->nitems, c->stream);
+    const int4* items = (c->opts.low_rank_threshold > 0.0 && c->items_lr) ? c->items_lr : c->items;
+    cudaError_t e = launch_items(c, tb, items, c->nitems, c->stream);
     if (e != cudaSuccess) return e;
     return launch_border(c, zin, out, zs, os, alpha);
 }
@@ -772,6 +777,55 @@ cudaError_t tc_chain_step_batch(ftq_ctx* b, const float* const* zin, float* cons
         e = launch_border(c, zin[s], out[s], j == p ? c->tab.h : nullptr, j == 1 ? c->tab.h : nullptr, 1.0f / j);
     }
     return e;
+}
+
+namespace {
+
+// Work list of a low-rank context: the items whose column tile starts below
+// the walker's rank (ws[12]), in the order of the full list, then -1 entries.
+__global__ void k_items_by_rank(const int4* __restrict__ all, int n, const double* __restrict__ ws, int NT,
+                                int4* __restrict__ out) {
+    __shared__ int base;
+    __shared__ int cnt[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += nt) {
+        const int i = c0 + tid;
+        int keep = 0;
+        int4 it = make_int4(-1, 0, 0, 0);
+        if (i < n) {
+            it = all[i];
+            keep = (double)(it.w * NT) < ws[(long)WSTRIDE * it.y + 12] ? 1 : 0;
+        }
+        cnt[tid] = keep;
+        __syncthreads();
+        // inclusive scan of the chunk's flags (Hillis-Steele)
+        for (int o = 1; o < nt; o <<= 1) {
+            const int v = tid >= o ? cnt[tid - o] : 0;
+            __syncthreads();
+            cnt[tid] += v;
+            __syncthreads();
+        }
+        if (keep) out[base + cnt[tid] - 1] = it;
+        __syncthreads();
+        if (tid == nt - 1) base += cnt[tid];
+        __syncthreads();
+    }
+    for (int i = base + tid; i < n; i += nt) out[i] = make_int4(-1, 0, 0, 0);
+}
+
+}  // namespace
+
+cudaError_t tc_items_by_rank(ftq_ctx* c) {
+    if (!c->items_lr) {
+        cudaError_t e = cudaMalloc(&c->items_lr, sizeof(int4) * (size_t)c->nitems);
+        if (e != cudaSuccess) return e;
+    }
+    int R, NT;
+    tc_plan(c->M, c->nct, &R, &NT);
+    k_items_by_rank<<<1, 1024, 0, c->stream>>>(c->items, c->nitems, c->wstate, NT, c->items_lr);
+    return cudaGetLastError();
 }
 
 // Work list of a batch: every member's items, largest basis first.

@@ -483,7 +483,7 @@ cudaError_t launch_force_bias_any(ftq_ctx* c, const double* x, const void* G, bo
 }
 
 cudaError_t launch_force_bias(ftq_ctx* c, const double* x) {
-    if (c->opts.precision != FTQ_FP64 && c->k > 0) return launch_force_bias_any(c, x, c->G32, true);
+    if (c->opts.precision != FTQ_FP64 && !c->g64_valid) return launch_force_bias_any(c, x, c->G32, true);
     return launch_force_bias_any(c, x, c->G, false);
 }
 

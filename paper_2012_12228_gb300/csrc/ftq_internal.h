@@ -102,6 +102,7 @@ struct ftq_ctx {
     int64_t wait_limit = -1;      // polls per mbarrier wait of the tensor-core chain (-1: default)
     int qr_nb = 0;                // panel width of the FP32 stabilisation QR (0: widest that fits)
     int4* items = nullptr;        // work list of the tensor-core chain
+    int4* items_lr = nullptr;     // the same, compacted by the walkers' ranks (low-rank mixed path)
     int nitems = 0;
     // ragged batch: member systems (owned), CUDA graph of the last propagation
     std::vector<ftq_ctx*> members;
@@ -242,6 +243,7 @@ cudaError_t tc_batch_items(ftq_ctx* b);
 cudaError_t tc_autotune(ftq_ctx* c, int* best_nct, float* best_ms);
 bool tc_supported(int M);
 cudaError_t tc_make_maps(ftq_ctx* c);
+cudaError_t tc_items_by_rank(ftq_ctx* c);
 cudaError_t tc_chain_step(ftq_ctx* c, const float* zin, float* out, const double* zs, const double* os,
                           float alpha);
 

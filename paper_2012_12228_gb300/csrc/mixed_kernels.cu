@@ -75,6 +75,23 @@ __global__ void k_planes_to_c128(const float* __restrict__ Ypl, double2* __restr
     Y[e] = make_double2((double)p[o] + (double)p[P.part + o], (double)p[o + P.Kp] + (double)p[P.part + o + P.Kp]);
 }
 
+// The complex128 chain (row-major) into the FP32 planes (tf32 hi + lo) and
+// the single FP32 plane beside them: the low-rank stabilisation's new Q.
+__global__ void k_c128_to_planes(const double2* __restrict__ Y, float* __restrict__ Ypl, float* __restrict__ Yf,
+                                 Planes P, int M, size_t wstride, long total) {
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    long w = e / ((long)M * M);
+    int ij = (int)(e % ((long)M * M));
+    int i = ij / M, c = ij % M;
+    const double2 y = Y[e];
+    const float2 v = make_float2((float)y.x, (float)y.y);
+    P.store(Ypl + wstride * w, i, c, v);
+    float* f = Yf + P.part * w + (size_t)c * (2 * P.Kp) + i;
+    f[0] = v.x;
+    f[P.Kp] = v.y;
+}
+
 __global__ void k_c64_to_c128(const float2* __restrict__ a, double2* __restrict__ b, long total) {
     long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (e >= total) return;
@@ -396,10 +413,47 @@ cudaError_t mixed_chain(ftq_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t mixed_qrcp(ftq_ctx* c) { return launch_qr_prepiv(c); }
+// The mixed chain as complex128 in c->Y (the low-rank path's factorisations
+// run in complex128 on it).
+cudaError_t planes_to_y64(ftq_ctx* c) {
+    const long n = (long)c->W * c->M * c->M;
+    LaunchScope ls(c, FTQ_K_BRIDGE);
+    k_planes_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->Ypl, c->Y, planes_of(c), c->M,
+                                                                     walker_stride(c), n);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_qrcp(ftq_ctx* c) {
+    if (c->opts.low_rank_threshold <= 0.0) return launch_qr_prepiv(c);
+    // low rank (Eq. thresh): the pivoted QR of the M x m panel and the
+    // truncation in complex128 on the chain's copy, the new Q back into the
+    // FP32 planes, and the tensor-core work list cut to the new ranks
+    cudaError_t e = planes_to_y64(c);
+    if (e == cudaSuccess) e = launch_qrcp_lr(c);            // c->Y <- Q, ranks -> ws[12]
+    if (e != cudaSuccess) return e;
+    {
+        const long n = (long)c->W * c->M * c->M;
+        LaunchScope ls(c, FTQ_K_BRIDGE);
+        k_c128_to_planes<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->Y, c->Ypl, c->Yf, planes_of(c),
+                                                                          c->M, walker_stride(c), n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && c->opts.precision == FTQ_MIXED) e = tc_items_by_rank(c);
+    return e;
+}
 
 cudaError_t mixed_green(ftq_ctx* c, int k) {
     const int M = c->M;
+    if (c->opts.low_rank_threshold > 0.0) {
+        // low rank: G(tau_k) and ln det by the Woodbury form in complex128 on
+        // the chain's copy (O(M m m_L) per walker), every slice
+        cudaError_t e = planes_to_y64(c);
+        if (e == cudaSuccess) e = launch_green64(c, c->Y, k, true);
+        if (e == cudaSuccess && k == c->sys.n_slices && c->opts.overlap == FTQ_OVERLAP_MODIFIED)
+            e = launch_green64(c, c->Y, k, true, true);
+        c->g64_valid = true;
+        return e;
+    }
     if (k == c->sys.n_slices) {
         // tau = beta: the final G and ln det in complex128
         const long n = (long)c->W * M * M;

@@ -84,7 +84,7 @@ def test_path_with_combing_matches_oracle_fp64(ftq):
         assert np.abs(G[w] - ref[w].G).max() < 1e-10 * np.abs(ref[w].G).max()
         assert bool(ws[w, 2] > 0.5) == ref[w].alive
         if ref[w].alive:
-            assert abs(ws[w, 0] - ref[w].logw.real) < 1e-9 * max(1.0, abs(ref[w].logw.real))
+            assert abs(ws[w, 0] - ref[w].logw.real) < 1e-10 * max(1.0, abs(ref[w].logw.real))
     with pytest.raises(ftq.FTQError):
         p.mu_grad()                                           # refused after a comb
     p.reset()
@@ -188,5 +188,5 @@ def test_path_with_pair_branching_matches_oracle_fp64(ftq):
         assert np.abs(G[w] - ref[w].G).max() < 1e-10 * np.abs(ref[w].G).max()
         assert bool(ws[w, 2] > 0.5) == ref[w].alive
         if ref[w].alive:
-            assert abs(ws[w, 0] - ref[w].logw.real) < 1e-9 * max(1.0, abs(ref[w].logw.real))
+            assert abs(ws[w, 0] - ref[w].logw.real) < 1e-10 * max(1.0, abs(ref[w].logw.real))
     p.close()
