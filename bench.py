@@ -186,7 +186,7 @@ TRAFFIC_PER_WALKER = {
 }
 
 
-def kernel_model(kind, M, W, precision):
+def kernel_model(kind, M, W, precision, green_tc=False):
     """(algorithmic flops of ONE launch, bound, peak TFLOP/s, peak source).
 
     Real flops; a complex multiply-add counts 8.  The tensor-core chain runs
@@ -205,7 +205,10 @@ def kernel_model(kind, M, W, precision):
         if precision == "mixed":
             return (3 * 8.0 * M ** 3 * W,) + tf32
         return (8.0 * M ** 3 * W,) + (fp64 if precision == "fp64" else fp32)
-    if kind == "green":          # LU (8/3 M^3) + two triangular solves with M right-hand sides (8 M^3)
+    if kind == "green":
+        if green_tc:             # Gauss-Jordan on [Mt^T | B^T]: 1.5 M^3 complex MACs, as 3xTF32 MMAs
+            return (3 * 12.0 * M ** 3 * W,) + tf32
+        # LU (8/3 M^3) + two triangular solves with M right-hand sides (8 M^3)
         return ((8.0 / 3.0 + 8.0) * M ** 3 * W,) + (fp64 if precision == "fp64" else fp32)
     if kind == "qrcp":
         if precision == "fp64":  # Householder QR (16/3) + forming Q (16/3) + T^-1 update (4)
@@ -216,19 +219,19 @@ def kernel_model(kind, M, W, precision):
     return None
 
 
-def roofline(prof, M, W, precision):
+def roofline(prof, M, W, precision, green_tc=False):
     timed = {k: v for k, v in prof.items() if v["n_timed"] > 0}
     dom = max(timed, key=lambda k: timed[k]["ms"])
     d = prof[dom]
     avg_s = d["ms"] / d["n_timed"] / 1e3
     share = d["ms"] / sum(v["ms"] for v in timed.values())
-    model = kernel_model(dom, M, W, precision)
+    model = kernel_model(dom, M, W, precision, green_tc)
     if model is None:
         return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
                 "traffic": None, "avg_launch_ms": avg_s * 1e3, "share_of_step": share}
     fl, bound, peak, src = model
     ach = fl / avg_s / 1e12
-    tr = TRAFFIC_PER_WALKER.get((precision, dom))
+    tr = None if (dom == "green" and green_tc) else TRAFFIC_PER_WALKER.get((precision, dom))
     out = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
            "traffic": None if tr is None else tr[0] * W, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
            "share_of_step": share}
@@ -257,7 +260,10 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     fields = torch.from_numpy(host).to(dev)
     out = {"M": M, "n_slices": n, "dtau": prop.query_f64("DTAU"), "walkers": W, "stab": stab, "p": p_order,
            "autotune": None if tuned is None else {"column_tiles": tuned[0], "ms_per_horner_step": tuned[1],
-                                                   "qr_panel": prop.query("QR_PANEL")}}
+                                                   "qr_panel": prop.query("QR_PANEL"),
+                                                   "green_kernel": {1: "tensor-core Gauss-Jordan",
+                                                                    2: "CUDA-core blocked LU"}.get(
+                                                       prop.query("GREEN_KERNEL"), "none")}}
 
     for s in range(warmup):
         prop.propagate(fields[s])
@@ -327,7 +333,7 @@ def measure_path(ftq, torch, dev, precision, W, steps, warmup, world, rank, barr
     prop.profile(False)
     prof = {k: {"ms": after[k][0], "n_timed": after[k][1] - before[k][1]} for k in after}
     out["kernel_ms_per_step"] = {k: v["ms"] for k, v in prof.items() if v["ms"] > 0}
-    out["roofline"] = roofline(prof, M, W, precision)
+    out["roofline"] = roofline(prof, M, W, precision, green_tc=prop.query("GREEN_KERNEL") == 1)
     out["device_status"] = prop.status()
     out["slice_average"] = measure_tracking(torch, prop, stream, fields)
     out["population_control"] = measure_comb(torch, prop, stream, precision, fields)

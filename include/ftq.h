@@ -248,8 +248,18 @@ int ftq_ranks(ftq_ctx* ctx, int* ranks_host);
  * unwritten); synchronises the stream. */
 int ftq_status(ftq_ctx* ctx, int* status_host);
 
+/* Choose the mixed path's kernel for G(tau_k), k < n (no counterpart in the
+ * paper, which computes G by one factorisation per slice): 0 by basis size
+ * (tensor cores from M = 384 up), 1 the tensor-core Gauss-Jordan kernel,
+ * 2 the CUDA-core blocked LU.  Both compute the same G, ln det and weights to
+ * FP32 accuracy; ftq_autotune sets the faster one.  No effect for FP64
+ * precision, FTQ_MIXED_SIMT (always the LU) or low rank.
+ * Errors: FTQ_EINVAL (NULL context or kind outside 0..2). */
+int ftq_set_green_kernel(ftq_ctx* ctx, int kind);
+
 /* Test hook of the failure detection (no counterpart in the paper): every
- * mbarrier wait of the tensor-core chain kernel (mixed precision) polls at
+ * mbarrier wait of the tensor-core kernels (mixed precision: the chain and
+ * the Gauss-Jordan G) polls at
  * most `polls` times before it gives up; -1 restores the default of 2^24
  * polls.  A wait that gives up latches FTQ_ETIMEOUT (read by ftq_status), the
  * kernel skips its remaining work, drains its own copies and MMAs with the
@@ -295,6 +305,9 @@ int ftq_slice_estimates(ftq_ctx* ctx, double* out_host, int capacity);
 #define FTQ_Q_PRECISION  6
 #define FTQ_Q_DEVICE_BYTES 7 /* device bytes owned by the context */
 #define FTQ_Q_QR_PANEL   8   /* panel width of the mixed path's FP32 QR (0: default) */
+#define FTQ_Q_GREEN_KERNEL 9 /* mixed path's G(tau) kernel for k < n: 1 tensor-core
+                                Gauss-Jordan, 2 CUDA-core blocked LU, 0 none (FP64
+                                precision or low rank) */
 int ftq_query(const ftq_ctx* ctx, int key, int64_t* value);
 
 /* Floating-point properties. */
@@ -334,11 +347,14 @@ int ftq_batch_propagate(ftq_ctx* batch, int n_slices, const double* const* field
 
 /* Time the candidate column tilings (1, 2 or 3 column tiles per 64-row
  * block) of the tensor-core chain on the context's own shapes and keep the
- * fastest, and likewise the panel width (32, 16 or 8 columns) of the FP32
- * Householder QR of the stabilisation; for a batch every member is tuned.
+ * fastest, likewise the panel width (32, 16 or 8 columns) of the FP32
+ * Householder QR of the stabilisation and the kernel of G(tau) (tensor-core
+ * Gauss-Jordan or CUDA-core blocked LU, FTQ_Q_GREEN_KERNEL); for a batch
+ * every member is tuned.
  * choice / ms: nullable host arrays (one entry per system) receiving the
  * chosen tile count and its time per Horner step.  Uses the scratch buffers
- * of the chain and of the stabilisation; walker state is not changed. */
+ * of the chain, of the stabilisation and of the estimators; walker state,
+ * G(tau) and the status word are not changed. */
 int ftq_autotune(ftq_ctx* ctx, int* choice, float* ms);
 
 /* Kernel classes for launch accounting and timing. */

@@ -11,7 +11,8 @@ import os
 FTQ_FP64, FTQ_MIXED, FTQ_MIXED_SIMT, FTQ_MIXED_F64UDT = 0, 1, 2, 3
 FTQ_PHASELESS, FTQ_FREE = 0, 1
 FTQ_OVERLAP_PAPER, FTQ_OVERLAP_MODIFIED = 0, 1
-_Q = dict(M=0, N_ALPHA=1, N_SLICES=2, SLICE=3, WALKERS=4, NCUT2=5, PRECISION=6, DEVICE_BYTES=7, QR_PANEL=8)
+_Q = dict(M=0, N_ALPHA=1, N_SLICES=2, SLICE=3, WALKERS=4, NCUT2=5, PRECISION=6, DEVICE_BYTES=7, QR_PANEL=8,
+          GREEN_KERNEL=9)
 _F = dict(BETA=0, DTAU=1, MU=2, MU_T=3, L=4, E_M=5)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -40,7 +41,7 @@ EXPORTS = ["ftq_init_ueg", "ftq_reset", "ftq_propagate_slices", "ftq_stabilise",
            "ftq_estimators", "ftq_weights", "ftq_status", "ftq_query", "ftq_query_f64",
            "ftq_basis", "ftq_transfers", "ftq_profile", "ftq_profile_read", "ftq_estimators_noalloc", "ftq_mu_grad",
            "ftq_init_batch", "ftq_batch_member", "ftq_batch_propagate", "ftq_autotune", "ftq_fields", "ftq_population_control", "ftq_structure_factor", "ftq_pair_branch",
-           "ftq_ranks", "ftq_set_wait_limit", "ftq_track_estimates", "ftq_slice_estimates",
+           "ftq_ranks", "ftq_set_wait_limit", "ftq_set_green_kernel", "ftq_track_estimates", "ftq_slice_estimates",
            "ftq_last_error", "ftq_destroy"]
 KERNELS = {"force_bias": 0, "chain": 1, "qrcp": 2, "green": 3, "estimators": 4, "init": 5, "bridge": 6,
            "border": 7, "fields": 8, "population": 9, "tinv": 10}
@@ -71,6 +72,7 @@ def load_library(path=None):
     lib.ftq_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ftq_ranks.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ftq_set_wait_limit.argtypes = [vp, ctypes.c_int64]
+    lib.ftq_set_green_kernel.argtypes = [vp, i]
     lib.ftq_track_estimates.argtypes = [vp, i]
     lib.ftq_slice_estimates.argtypes = [vp, dp, i]
     lib.ftq_query.argtypes = [vp, i, i64p]
@@ -148,7 +150,8 @@ class Propagator:
         return obj
 
     def autotune(self):
-        """Pick the column tiling of the tensor-core chain by timing; returns (tiles, ms per step)."""
+        """Pick the column tiling of the tensor-core chain, the QR panel width and the G(tau)
+        kernel by timing; returns (tiles, ms per Horner step)."""
         ch = (ctypes.c_int * 1)()
         ms = (ctypes.c_float * 1)()
         self._check(self.lib.ftq_autotune(self.h, ch, ms), "ftq_autotune")
@@ -346,8 +349,12 @@ class Propagator:
                 "alive": r[:, 5].astype(int), "E_avg": complex(a[0, 1], a[0, 2]),
                 "N_avg": complex(a[0, 3], a[0, 4])}
 
+    def set_green_kernel(self, kind):
+        """Mixed path's G(tau) kernel: 0 by basis size, 1 tensor cores (Gauss-Jordan), 2 CUDA cores (LU)."""
+        self._check(self.lib.ftq_set_green_kernel(self.h, int(kind)), "ftq_set_green_kernel")
+
     def set_wait_limit(self, polls):
-        """Test hook: polls per mbarrier wait of the tensor-core chain (-1: default)."""
+        """Test hook: polls per mbarrier wait of the tensor-core kernels (-1: default)."""
         self._check(self.lib.ftq_set_wait_limit(self.h, int(polls)), "ftq_set_wait_limit")
 
     def status(self):

@@ -40,7 +40,7 @@ cudaError_t upload(ftq_ctx* c, T** p, const std::vector<T>& v) {
 
 void free_all(ftq_ctx* c) {
     void* ptrs[] = {c->Y, c->Tinv, c->G, c->work, c->work2, c->zbuf[0], c->zbuf[1], c->DR, c->phi,
-                    c->Ypl, c->zpl[0], c->zpl[1], c->G32, c->w32, c->w2_32,
+                    c->Ypl, c->zpl[0], c->zpl[1], c->G32, c->w32,
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
                     c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
@@ -135,8 +135,11 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         chk(dalloc(c, &c->zpl[0], W * wsz));
         chk(dalloc(c, &c->zpl[1], W * wsz));
         chk(dalloc(c, &c->G32, W * MM));
-        chk(dalloc(c, &c->w32, W * MM));
-        chk(dalloc(c, &c->w2_32, W * MM));
+        // one allocation: the LU and solve halves for the QR and blocked LU
+        // kernels, or per walker one contiguous M x 2M complex block for the
+        // tensor-core Gauss-Jordan Green kernel
+        chk(dalloc(c, &c->w32, W * std::max(2 * MM, (ftq::green_tc_floats(M) + 1) / 2)));
+        c->w2_32 = c->w32 + W * MM;
         chk(dalloc(c, &c->xsum, W * MM));
     }
     chk(dalloc(c, &c->Tinv, W * MM));
@@ -436,6 +439,13 @@ int ftq_status(ftq_ctx* c, int* status_host) {
     return FTQ_OK;
 }
 
+int ftq_set_green_kernel(ftq_ctx* c, int kind) {
+    if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
+    if (kind < 0 || kind > 2) return fail(c, FTQ_EINVAL, "green kernel must be 0, 1 or 2");
+    c->green_kind = kind;
+    return FTQ_OK;
+}
+
 int ftq_set_wait_limit(ftq_ctx* c, int64_t polls) {
     if (!c) return fail(nullptr, FTQ_EINVAL, "ctx is NULL");
     if (polls < -1) return fail(c, FTQ_EINVAL, "polls must be >= -1");
@@ -455,6 +465,10 @@ int ftq_query(const ftq_ctx* c, int key, int64_t* value) {
         case FTQ_Q_PRECISION: *value = c->opts.precision; break;
         case FTQ_Q_DEVICE_BYTES: *value = (int64_t)c->bytes; break;
         case FTQ_Q_QR_PANEL: *value = c->qr_nb; break;
+        case FTQ_Q_GREEN_KERNEL:
+            *value = (c->opts.precision == FTQ_FP64 || c->opts.low_rank_threshold > 0.0) ? 0
+                     : (ftq::green_uses_tc(c) ? 1 : 2);
+            break;
         default: return fail(const_cast<ftq_ctx*>(c), FTQ_EINVAL, "unknown query key");
     }
     return FTQ_OK;

@@ -174,6 +174,8 @@ int ftq_autotune(ftq_ctx* c, int* choice, float* ms) {
         int qnb = 0;
         float qms = 0.f;
         if (e == cudaSuccess) e = ftq::qr_autotune(m, &qnb, &qms);
+        float gtc = 0.f, glu = 0.f;
+        if (e == cudaSuccess) e = ftq::green_autotune(m, &gtc, &glu);
         if (e != cudaSuccess) return bfail(c, FTQ_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
         if (choice) choice[s] = best;
         if (ms) ms[s] = bms;

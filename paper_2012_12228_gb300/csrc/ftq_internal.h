@@ -93,7 +93,7 @@ struct ftq_ctx {
     float* zpl[2] = {nullptr, nullptr};
     float2* G32 = nullptr;        // G(tau_k) for k < n, complex64            [W][M][M]
     float2* w32 = nullptr;        // FP32 LU workspace                        [W][M][M]
-    float2* w2_32 = nullptr;      // FP32 solve workspace                     [W][M][M]
+    float2* w2_32 = nullptr;      // FP32 solve workspace = w32 + W M M       [W][M][M]
     bool g64_valid = true;        // G holds the current G(tau) (mixed: only at k = 0, n)
     // TMA descriptors (CUtensorMap, 128 bytes) of the three chain buffers
     alignas(64) unsigned char tmap[3][128] = {};
@@ -101,6 +101,7 @@ struct ftq_ctx {
     int nct = 1;                  // column tiles of the tensor-core chain (autotuned)
     int64_t wait_limit = -1;      // polls per mbarrier wait of the tensor-core chain (-1: default)
     int qr_nb = 0;                // panel width of the FP32 stabilisation QR (0: widest that fits)
+    int green_kind = 0;           // mixed Green kernel: 0 by basis size, 1 tensor cores, 2 CUDA cores
     int4* items = nullptr;        // work list of the tensor-core chain
     int4* items_lr = nullptr;     // the same, compacted by the walkers' ranks (low-rank mixed path)
     int nitems = 0;
@@ -230,7 +231,13 @@ cudaError_t launch_mu_grad(ftq_ctx* c, double* per_walker);
 // Blocked FP32 Green's function (green_blocked.cu); used while its shared
 // memory fits.
 size_t green32b_smem(int M);
-cudaError_t launch_green32b(ftq_ctx* c, int k);
+cudaError_t launch_green32b(ftq_ctx* c, int k, float2* G = nullptr, double* ws = nullptr);
+size_t green_tc_smem(int M, int NT);
+size_t green_tc_floats(int M);   // workspace floats per walker of the tensor-core Green kernel
+int green_tc_tile(int M);
+cudaError_t launch_green_tc(ftq_ctx* c, int k, float2* G = nullptr, double* ws = nullptr);
+bool green_uses_tc(const ftq_ctx* c);
+cudaError_t green_autotune(ftq_ctx* c, float* ms_tc, float* ms_lu);
 
 // Pre-pivoted stabilisation of the mixed chain (qr_mixed.cu).
 cudaError_t launch_qr_prepiv(ftq_ctx* c);

@@ -21,6 +21,7 @@
 
 #include "complex_math.cuh"
 #include "ftq_internal.h"
+#include "green_tail.cuh"
 #include "mixed_common.cuh"
 
 namespace ftq {
@@ -33,7 +34,6 @@ constexpr int TILE = 32 * 33;  // one padded 32 x 32 transpose tile
 // Length of the U12 region, which also holds the transpose tile.
 __host__ __device__ __forceinline__ int us_len(int M) { return NB * M > TILE ? NB * M : TILE; }
 constexpr int GT_MAX = 288;
-constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ float2 csub_mul(float2 acc, float2 a, float2 b) {
     // acc - a * b
@@ -418,40 +418,8 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
         trg = trg + make_double2(g.x, g.y);
     }
     trg = bsum(trg, shc);
-    if (tid == 0) {
-        double* s = ws + (long)WSTRIDE * w;
-        double2 ld = ldm;
-        ld.x -= lsum;
-        ld.y += kPi * (double)(nswap ^ ((int)s[7]));
-        if (!isfinite(ld.x) || !isfinite(ld.y)) atomicOr(status, 1);
-        // d ln det(I + A_k)/dmu = k dtau (M - tr G(tau_k)): every B carries exp(dtau mu)
-        const double2 tk = make_double2(kdt * ((double)M - trg.x), -kdt * trg.y);
-        const double2 dlnS = make_double2(2.0 * (tk.x - s[9]), 2.0 * (tk.y - s[10]));
-        double2 lnS = make_double2(2.0 * (ld.x - s[3]), 2.0 * (ld.y - s[4]));
-        double gr = s[5], gi = s[6];
-        if (constraint == FTQ_FREE) {
-            s[0] += lnS.x + gr;
-            s[1] = remainder(s[1] + lnS.y + gi, 2.0 * kPi);
-            s[8] += dlnS.x;
-            s[11] += dlnS.y;
-        } else if (s[2] > 0.5) {
-            const double cth = cos(lnS.y);
-            if (!isfinite(lnS.x + gr) || !(cth == cth)) {
-                // a non-finite ratio or Gaussian factor drops the walker (weight 0)
-                s[2] = 0.0;
-                atomicOr(status, 1);
-            } else if (cth <= 0.0) {
-                s[2] = 0.0;
-            } else {
-                s[0] += lnS.x + gr + log(cth);
-                s[8] += dlnS.x - tan(lnS.y) * dlnS.y;   // d log cos(theta) = -tan(theta) d theta
-            }
-        }
-        s[3] = ld.x;
-        s[4] = remainder(ld.y, 2.0 * kPi);
-        s[9] = tk.x;
-        s[10] = tk.y;
-    }
+    if (tid == 0)
+        green_weight_tail(ws + (long)WSTRIDE * w, ldm, lsum, nswap, trg, M, kdt, constraint, status);
 }
 
 }  // namespace
@@ -460,7 +428,7 @@ size_t green32b_smem(int M) {
     return ((size_t)M * PSTR + us_len(M)) * sizeof(float2) + (size_t)M * (2 * sizeof(float2) + 3 * sizeof(float) + 2 * sizeof(int));
 }
 
-cudaError_t launch_green32b(ftq_ctx* c, int k) {
+cudaError_t launch_green32b(ftq_ctx* c, int k, float2* G, double* ws) {
     const int M = c->M;
     const size_t sm = green32b_smem(M);
     static size_t sm_set = 0;
@@ -476,7 +444,8 @@ cudaError_t launch_green32b(ftq_ctx* c, int k) {
     int nt = (M + 31) / 32 * 32;
     nt = nt < 256 ? 256 : (nt > GT_MAX ? GT_MAX : nt);
     LaunchScope ls(c, FTQ_K_GREEN);
-    k_green32b<<<c->W, nt, sm, c->stream>>>(c->Ypl, c->Tinv, c->DR, c->w32, c->w2_32, c->G32, c->tab.eps, c->wstate,
+    k_green32b<<<c->W, nt, sm, c->stream>>>(c->Ypl, c->Tinv, c->DR, c->w32, c->w2_32, G ? G : c->G32, c->tab.eps,
+                                           ws ? ws : c->wstate,
                                            c->status, M, lscale, c->sys.mu_T, c->opts.constraint, P, 2 * P.part,
                                            (double)k * c->sys.dtau);
     return cudaGetLastError();

@@ -468,6 +468,12 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
         c->g64_valid = true;
         return e;
     }
+    if (green_uses_tc(c)) {
+        // rank-16 Gauss-Jordan updates on the tensor cores
+        cudaError_t e = launch_green_tc(c, k);
+        c->g64_valid = false;
+        return e;
+    }
     if (green32b_smem(M) <= 220 * 1024) {
         cudaError_t e = launch_green32b(c, k);
         c->g64_valid = false;
@@ -483,6 +489,61 @@ cudaError_t mixed_green(ftq_ctx* c, int k) {
                                           walker_stride(c), (double)k * c->sys.dtau);
     c->g64_valid = false;
     return cudaGetLastError();
+}
+
+// Which Green kernel the mixed path runs for slices k < n.  The tensor-core
+// Gauss-Jordan kernel streams S = [Mt^T | B^T] once per 16-column panel, the
+// CUDA-core blocked LU computes in shared-memory panels with four walkers per
+// SM; measured per 5-slice block on a GB300: M = 257, 1024 walkers: 96.7 ms
+// (tensor cores) vs 63.6 ms (LU); M = 515, 152 walkers: 86.5 vs 149.1 ms.
+// Without a measurement the crossover is taken between the two basis sizes;
+// ftq_autotune times both on the context's own workload.
+constexpr int GREEN_TC_MIN_M = 384;
+
+bool green_uses_tc(const ftq_ctx* c) {
+    if (c->opts.precision == FTQ_MIXED_SIMT || green_tc_tile(c->M) == 0) return false;
+    if (c->green_kind == 1) return true;
+    if (c->green_kind == 2) return false;
+    return c->M >= GREEN_TC_MIN_M;
+}
+
+// Time one launch of each Green kernel (after one warm-up launch) on the
+// context's current chain, writing G and the weights into scratch buffers
+// (zbuf[0] and est), so that neither G(tau) nor the walker state changes.
+cudaError_t green_autotune(ftq_ctx* c, float* ms_tc, float* ms_lu) {
+    *ms_tc = *ms_lu = 0.f;
+    if (c->opts.precision == FTQ_MIXED_SIMT || c->opts.low_rank_threshold > 0.0 || green_tc_tile(c->M) == 0)
+        return cudaSuccess;
+    float2* gs = reinterpret_cast<float2*>(c->zbuf[0]);
+    double* ws = c->est;
+    const size_t wbytes = sizeof(double) * WSTRIDE * (size_t)c->W;
+    int saved_status = 0;
+    cudaError_t e = cudaMemcpyAsync(&saved_status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int k = c->k < c->sys.n_slices ? c->k + 1 : 1;
+    for (int kind = 1; kind <= 2 && e == cudaSuccess; ++kind) {
+        auto run = [&]() { return kind == 1 ? launch_green_tc(c, k, gs, ws) : launch_green32b(c, k, gs, ws); };
+        e = cudaMemcpyAsync(ws, c->wstate, wbytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = run();                          // warm-up
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ws, c->wstate, wbytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        (kind == 1 ? *ms_tc : *ms_lu) = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the trial inputs are whatever the chain holds; a flag they raise is not the caller's
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->status, &saved_status, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) c->green_kind = *ms_tc < *ms_lu ? 1 : 2;
+    return e;
 }
 
 cudaError_t mixed_sync_g64(ftq_ctx* c) {
