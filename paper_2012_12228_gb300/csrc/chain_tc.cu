@@ -66,6 +66,7 @@ struct TcArgs {
 };
 
 constexpr int MAXSYS = 8;
+constexpr int NSMAX = 4;             // most k-tile stages the pipeline keeps in flight
 
 // Up to MAXSYS systems in one launch: their chain tensor maps and arguments.
 struct TcBatch {
@@ -77,6 +78,7 @@ struct TcBatch {
     int qsize_max;
     int m_max;
     int ncols;          // TMEM columns allocated once per CTA
+    int nstage;         // shared-memory stages of the k-tile pipeline (2 .. NSMAX)
     long long wait_limit;   // polls per bounded mbarrier wait of the pipeline
 };
 
@@ -130,7 +132,7 @@ __device__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort
 __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_constant__ TcBatch tb,
                                                              const int4* __restrict__ items, int nitems) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t tma_bar[2], mma_bar[2], afull[2], tfull[2], tempty[2];
+    __shared__ uint64_t tma_bar[NSMAX], mma_bar[NSMAX], afull[NSMAX], tfull[2], tempty[2];
     __shared__ uint32_t tmem_sh;
     __shared__ volatile int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -139,16 +141,19 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
     const uint32_t a_bytes = AROWS * KTILE * 4;
     const uint32_t bmax_bytes = (uint32_t)tb.nt_max * KTILE * 4;
     const uint32_t stage_bytes = 2 * a_bytes + 2 * bmax_bytes;
-    float2* phs = reinterpret_cast<float2*>(base + 2 * stage_bytes);
+    const int NS = tb.nstage;
+    float2* phs = reinterpret_cast<float2*>(base + (size_t)NS * stage_bytes);
     int* pks = reinterpret_cast<int*>(phs + tb.nslot_max);
     uint16_t* qs = reinterpret_cast<uint16_t*>(pks + tb.m_max);
     int* st = tb.args[0].status;
 
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NSMAX; ++b) {
             mbar_init(&tma_bar[b], 1);
             mbar_init(&mma_bar[b], 1);
             mbar_init(&afull[b], NGEN / 32);
+        }
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], NEPI / 32);
         }
@@ -164,23 +169,35 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
     if (warp == (NEPI + NGEN) / 32) {
         // ------------------------------------------------ control warp
         if (lane == 0) {
-            int g = 0, last_tma = -1, last_mma = -1;
-            auto issue_tma = [&](int4 it, int kt, int gi) {
+            int g = 0, last_mma = -1;
+            int last_tma[NSMAX];
+#pragma unroll
+            for (int b = 0; b < NSMAX; ++b) last_tma[b] = -1;
+            // prefetch cursor: the next k tile (over all items of this CTA)
+            // whose B tile is to be loaded, and its global index pf_g
+            int pf_item = blockIdx.x, pf_kt = 0, pf_g = 0;
+            auto pf_valid = [&]() { return pf_item < nitems && items[pf_item].x >= 0; };
+            auto prefetch = [&]() {
+                const int4 it = items[pf_item];
                 const TcArgs& q = tb.args[it.x];
-                const int sg = gi & 1;
+                const int sg = pf_g % NS;
                 unsigned char* Bh = base + sg * stage_bytes + 2 * a_bytes;
                 mbar_expect_tx(&tma_bar[sg], 2u * (uint32_t)q.NT * KTILE * 4);
-                tma_load_2d(Bh, &tb.maps[it.x], kt * KTILE, (2 * it.y) * q.LDc + it.w * q.NT, &tma_bar[sg]);
-                tma_load_2d(Bh + bmax_bytes, &tb.maps[it.x], kt * KTILE, (2 * it.y + 1) * q.LDc + it.w * q.NT,
+                tma_load_2d(Bh, &tb.maps[it.x], pf_kt * KTILE, (2 * it.y) * q.LDc + it.w * q.NT, &tma_bar[sg]);
+                tma_load_2d(Bh + bmax_bytes, &tb.maps[it.x], pf_kt * KTILE, (2 * it.y + 1) * q.LDc + it.w * q.NT,
                             &tma_bar[sg]);
-                last_tma = gi;
+                last_tma[sg] = pf_g;
+                ++pf_g;
+                if (++pf_kt == q.ktiles) {
+                    pf_kt = 0;
+                    pf_item += gridDim.x;
+                }
             };
             bool ok = true;
-            if ((int)blockIdx.x < nitems && items[blockIdx.x].x >= 0) issue_tma(items[blockIdx.x], 0, 0);
+            while (pf_g < NS - 1 && pf_valid()) prefetch();      // NS - 1 tiles ahead
             int li = 0;                                   // items of this CTA so far
             for (int item = blockIdx.x; item < nitems && ok && items[item].x >= 0; item += gridDim.x, ++li) {
                 const int4 it = items[item];
-                const int4 nx = item + (int)gridDim.x < nitems ? items[item + gridDim.x] : make_int4(0, 0, 0, 0);
                 const TcArgs& p = tb.args[it.x];
                 const uint32_t idesc = idesc_tf32(p.NT);
                 const int tb_i = li & 1;
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                 // the epilogue of item li - 2 must have released this buffer
                 if (li >= 2) ok = mbar_wait_ab(&tempty[tb_i], (uint32_t)(((li - 2) >> 1) & 1), &abort_sh, st, tb.wait_limit);
                 for (int kt = 0; kt < p.ktiles && ok; ++kt, ++g) {
-                    const int s = g & 1, use = g >> 1;
+                    const int s = g % NS, use = g / NS;
                     ok = mbar_wait_ab(&afull[s], (uint32_t)(use & 1), &abort_sh, st, tb.wait_limit) &&
                          mbar_wait_ab(&tma_bar[s], (uint32_t)(use & 1), &abort_sh, st, tb.wait_limit);
                     if (!ok) break;
@@ -206,16 +223,21 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                     mma_commit(&mma_bar[s]);
                     if (kt + 1 == p.ktiles) mma_commit(&tfull[tb_i]);   // accumulator complete
                     last_mma = g;
-                    // MMA(g - 1) frees stage s ^ 1 for the next B tile
-                    if (g >= 1) ok = mbar_wait_ab(&mma_bar[s ^ 1], (uint32_t)(((g - 1) >> 1) & 1), &abort_sh, st, tb.wait_limit);
-                    if (!ok) break;
-                    if (kt + 1 < p.ktiles) issue_tma(it, kt + 1, g + 1);
-                    else if (item + (int)gridDim.x < nitems && nx.x >= 0) issue_tma(nx, 0, g + 1);
+                    // the next B tile goes into the stage of tile pf_g - NS
+                    // (= g - 1 in steady state), once its MMAs are done
+                    if (pf_valid()) {
+                        if (pf_g >= NS)
+                            ok = mbar_wait_ab(&mma_bar[pf_g % NS], (uint32_t)(((pf_g - NS) / NS) & 1), &abort_sh, st,
+                                              tb.wait_limit);
+                        if (!ok) break;
+                        prefetch();
+                    }
                 }
             }
             if (!ok) {   // abort latched: drain this CTA's own copies and MMAs
-                if (last_tma >= 0) mbar_wait(&tma_bar[last_tma & 1], (uint32_t)((last_tma >> 1) & 1));
-                if (last_mma >= 0) mbar_wait(&mma_bar[last_mma & 1], (uint32_t)((last_mma >> 1) & 1));
+                for (int b = 0; b < NS; ++b)
+                    if (last_tma[b] >= 0) mbar_wait(&tma_bar[b], (uint32_t)((last_tma[b] / NS) & 1));
+                if (last_mma >= 0) mbar_wait(&mma_bar[last_mma % NS], (uint32_t)((last_mma / NS) & 1));
             }
         }
     } else if (warp >= NEPI / 32) {
@@ -247,8 +269,8 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1) k_chain_tc(const __grid_consta
                 prow[t] = i < p.M ? pks[i] + p.qoff : -1;
             }
             for (int kt = 0; kt < p.ktiles; ++kt, ++g) {
-                const int s = g & 1, use = g >> 1;
-                if (g >= 2 && !mbar_wait_ab(&mma_bar[s], (uint32_t)((use - 1) & 1), &abort_sh, st, tb.wait_limit)) continue;
+                const int s = g % NS, use = g / NS;
+                if (g >= NS && !mbar_wait_ab(&mma_bar[s], (uint32_t)((use - 1) & 1), &abort_sh, st, tb.wait_limit)) continue;
                 if (abort_sh) continue;
                 unsigned char* Ahi = base + s * stage_bytes;
                 unsigned char* Alo = Ahi + a_bytes;
@@ -482,20 +504,30 @@ void tc_plan(int M, int nct, int* R, int* NT) {
     else *NT = 256;                                     // border columns [256 nct, M) on CUDA cores
 }
 
-// Dynamic shared memory of k_chain_tc: two stages of A (hi, lo) and B
+// Dynamic shared memory of k_chain_tc: nstage stages of A (hi, lo) and B
 // (hi, lo) tiles, the field table, the packed basis and the difference cube.
-size_t tc_smem_bytes(int nt_max, int nslot_max, int m_max, int qsize_max) {
+size_t tc_smem_bytes(int nt_max, int nslot_max, int m_max, int qsize_max, int nstage) {
     const size_t stage = 2 * (size_t)AROWS * KTILE * 4 + 2 * (size_t)nt_max * KTILE * 4;
-    return 1024 + 2 * stage + sizeof(float2) * nslot_max + sizeof(int) * m_max + sizeof(uint16_t) * qsize_max;
+    return 1024 + (size_t)nstage * stage + sizeof(float2) * nslot_max + sizeof(int) * m_max +
+           sizeof(uint16_t) * qsize_max;
 }
 
 constexpr size_t TC_SMEM_LIMIT = 227 * 1024 - 2048;   // leaves room for the kernel's static shared memory
+
+// The deepest pipeline (2 .. NSMAX stages) whose shared memory fits; 0 when
+// not even two stages do.  More stages keep more B tiles in flight, which
+// hides the TMA latency behind the MMAs of the tiles before.
+int tc_stages(int nt_max, int nslot_max, int m_max, int qsize_max) {
+    for (int ns = NSMAX; ns >= 2; --ns)
+        if (tc_smem_bytes(nt_max, nslot_max, m_max, qsize_max, ns) <= TC_SMEM_LIMIT) return ns;
+    return 0;
+}
 
 bool tc_fits(const ftq_ctx* c, int nct) {
     int R, NT;
     tc_plan(c->M, nct, &R, &NT);
     const int qsize = c->sys.qS * c->sys.qS * c->sys.qS;
-    return tc_smem_bytes(NT, c->nslot, c->M, qsize) <= TC_SMEM_LIMIT;
+    return tc_stages(NT, c->nslot, c->M, qsize) >= 2;
 }
 
 // The fewest column tiles (1 .. 8) whose tile width lets the shared memory
@@ -586,12 +618,10 @@ bool fill_args(ftq_ctx* c, const float* zin, float* out, const double* zs, const
     return true;
 }
 
-size_t tc_smem(int nt_max, int nslot_max, int m_max, int qsize_max) {
-    return tc_smem_bytes(nt_max, nslot_max, m_max, qsize_max);
-}
-
-cudaError_t launch_items(ftq_ctx* timing_ctx, const TcBatch& tb, const int4* items, int nitems, cudaStream_t st) {
-    const size_t smem = tc_smem(tb.nt_max, tb.nslot_max, tb.m_max, tb.qsize_max);
+cudaError_t launch_items(ftq_ctx* timing_ctx, TcBatch& tb, const int4* items, int nitems, cudaStream_t st) {
+    tb.nstage = tc_stages(tb.nt_max, tb.nslot_max, tb.m_max, tb.qsize_max);
+    if (tb.nstage < 2) return cudaErrorInvalidValue;
+    const size_t smem = tc_smem_bytes(tb.nt_max, tb.nslot_max, tb.m_max, tb.qsize_max, tb.nstage);
     static size_t smem_set = 0;
     cudaError_t e = cudaSuccess;
     if (smem > smem_set) {
