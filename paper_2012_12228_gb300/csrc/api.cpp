@@ -43,7 +43,7 @@ void free_all(ftq_ctx* c) {
                     c->Ypl, c->zpl[0], c->zpl[1], c->G32, c->w32,
                     c->hh, c->htau, c->perm, c->wstate, c->est, c->red, c->status,
                     c->tab.vidx, c->tab.pair_ptr, c->tab.pair_a, c->tab.pair_b, c->tab.eps, c->tab.h,
-                    c->tab.cq, c->tab.vq, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
+                    c->tab.cq, c->tab.vq, c->tab.vqf, c->tab.ksq, c->tab.g0, c->items, c->tab.pk, c->tab.qcube,
                     c->tab.hf, c->phi32, c->xbuf, c->xsum, c->pc_w, c->pc_cnt, c->pc_parent, c->pc_pairs,
                     c->sq_walker, c->sq_w, c->sq_out, c->Yf, c->tab.eplus, c->trk, c->trk_out, c->items_lr};
     for (void* p : ptrs)
@@ -182,6 +182,14 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         chk(upload(c, &c->tab.h, h));
         chk(upload(c, &c->tab.cq, s.cq));
         chk(upload(c, &c->tab.vq, s.vq));
+        {
+            std::vector<float2> vqf(s.vq.size());
+            for (size_t q = 0; q < s.vq.size(); ++q) {
+                vqf[q].x = (float)s.vq[q];
+                vqf[q].y = (float)(s.vq[q] - (double)vqf[q].x);
+            }
+            chk(upload(c, &c->tab.vqf, vqf));
+        }
         chk(upload(c, &c->tab.ksq, ksq));
         chk(upload(c, &c->tab.g0, g0));
         chk(upload(c, &c->tab.pk, s.pk));
@@ -192,9 +200,11 @@ int ftq_init_ueg(ftq_ctx** out, int N, int M, double rs, double theta, double mu
         }
         chk(upload(c, &c->tab.hf, hf));
         chk(upload(c, &c->tab.qcube, s.qcube));
-        std::vector<int> eplus;                 // pairs of the odd (+Q) slots
+        // exchange work units: chunks of 32 pairs of every odd (+Q) slot
+        std::vector<int4> eplus;
         for (int sl = 1; sl < c->nslot; sl += 2)
-            for (int e = s.pair_ptr[sl]; e < s.pair_ptr[sl + 1]; ++e) eplus.push_back(e);
+            for (int e = s.pair_ptr[sl]; e < s.pair_ptr[sl + 1]; e += 32)
+                eplus.push_back(make_int4(s.pair_ptr[sl], s.pair_ptr[sl + 1], e, (sl - 1) >> 1));
         c->tab.neplus = (int)eplus.size();
         chk(upload(c, &c->tab.eplus, eplus));
     }

@@ -60,12 +60,15 @@ struct DevTables {
     double* h = nullptr;          // exp(-dtau/2 (eps + deps - mu)) [M]
     double* cq = nullptr;         // [nq_half]
     double* vq = nullptr;         // [nq_half]
+    float2* vqf = nullptr;        // [nq_half] v_Q as a float pair (hi, lo)
     double* ksq = nullptr;        // |K|^2 [M]
     double* g0 = nullptr;         // diagonal of G(0) = (I + B_T^n)^-1 [M]
     int* pk = nullptr;            // packed basis coordinates [M]
     float2* hf = nullptr;         // h as float pairs (hi, lo) [M]
     uint16_t* qcube = nullptr;    // difference -> slot [S^3]
-    int* eplus = nullptr;         // the pairs of the half-space transfers (odd slots)
+    int4* eplus = nullptr;        // exchange work units: per half-space transfer (odd slot) and chunk
+                                  // of 32 of its pairs, {first, end of the slot's pair list, first pair
+                                  // of the chunk, index into v_Q}
     int neplus = 0;
 };
 
