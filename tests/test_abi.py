@@ -59,6 +59,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ftq_init_ueg(ctypes.byref(h), 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
     assert lib.ftq_init_ueg(None, 2, 7, 1.0, 0.5, math.nan, 0.05, ctypes.byref(o)) == -1
     assert lib.ftq_set_wait_limit(None, 0) == -1
+    assert lib.ftq_set_green_kernel(None, 1) == -1
     lib.ftq_destroy(None)
 
 
