@@ -74,21 +74,26 @@ def test_nan_field_latches_numeric_status(ftq, prec):
     p.close()
 
 
-def test_chain_wait_that_runs_out_latches_timeout(ftq):
-    """The tensor-core chain's bounded mbarrier waits, cut to zero polls by the
-    test hook, give up at once: the launch latches FTQ_ETIMEOUT, skips its
-    work, drains its own copies with the normal bound and frees its tensor
-    memory; after a reset the same context reproduces a clean run exactly.
+@pytest.mark.parametrize("green_kernel", [2, 1])
+def test_chain_wait_that_runs_out_latches_timeout(ftq, green_kernel):
+    """The tensor-core kernels' bounded mbarrier waits, cut to zero polls by
+    the test hook, give up at once: the launch latches FTQ_ETIMEOUT, skips its
+    work, drains its own copies and MMAs with the normal bound and frees its
+    tensor memory; after a reset the same context reproduces a clean run
+    exactly.  With green_kernel = 1 the slice's G(tau) also comes from the
+    tensor-core Gauss-Jordan kernel, whose MMA wait gives up the same way.
     (N=2, M=7, 4 walkers: the smallest launch.)"""
     c = WORKLOADS["ueg_n2_m7"]
     W, n = 4, 6
     ref = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, precision=ftq.FTQ_MIXED)
+    ref.set_green_kernel(green_kernel)
     f = torch.from_numpy(gaussian_fields(c["seed"], n, W, ref.n_alpha)).cuda()
     ref.propagate(f)
     G0, w0 = ref.green().cpu().numpy(), ref.weights().cpu().numpy()
     assert ref.status() == 0
     ref.close()
     p = ftq.Propagator(c["N"], c["M"], c["rs"], c["theta"], c["dtau"], walkers=W, precision=ftq.FTQ_MIXED)
+    p.set_green_kernel(green_kernel)
     p.set_wait_limit(0)
     p.propagate(f[:1].contiguous())
     torch.cuda.synchronize()
