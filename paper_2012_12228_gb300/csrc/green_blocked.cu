@@ -28,6 +28,7 @@ namespace ftq {
 namespace {
 
 constexpr int NB = 8;
+constexpr int SU = 8;          // rows of X loaded per step of the solves (loads in flight per thread)
 constexpr int PSTR = NB + 1;   // padded row stride of the LU panel (column reads conflict-free)
 constexpr int TILE = 32 * 33;  // one padded 32 x 32 transpose tile
 
@@ -319,14 +320,14 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
 #pragma unroll
             for (int q = 0; q < NB; ++q)
                 s[q] = q < nb ? cmul(P.load(Yw, i, jb + q), drs[jb + q]) : make_float2(0.f, 0.f);
-            for (int m = 0; m < jb; m += 4) {
-                float2 x[4];
+            for (int m = 0; m < jb; m += SU) {   // jb is a multiple of NB = SU
+                float2 x[SU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) x[u] = X[(long)(m + u) * M + i];
+                for (int u = 0; u < SU; ++u) x[u] = X[(long)(m + u) * M + i];
 #pragma unroll
                 for (int q = 0; q < NB; ++q)      // no guard: columns q >= nb are zero
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) s[q] = csub_mul(s[q], x[u], Ps[(m + u) * NB + q]);
+                    for (int u = 0; u < SU; ++u) s[q] = csub_mul(s[q], x[u], Ps[(m + u) * NB + q]);
             }
 #pragma unroll
             for (int q = 0; q < NB; ++q)
@@ -359,14 +360,14 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
             for (int q = 0; q < NB; ++q)
                 s[q] = q < nb ? X[(long)(jb + q) * M + i] : make_float2(0.f, 0.f);
             int m = jb + nb;
-            for (; m + 4 <= M; m += 4) {
-                float2 x[4];
+            for (; m + SU <= M; m += SU) {
+                float2 x[SU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) x[u] = X[(long)(m + u) * M + i];
+                for (int u = 0; u < SU; ++u) x[u] = X[(long)(m + u) * M + i];
 #pragma unroll
                 for (int q = 0; q < NB; ++q)      // no guard: columns q >= nb are zero
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) s[q] = csub_mul(s[q], x[u], Ps[(m + u - jb) * NB + q]);
+                    for (int u = 0; u < SU; ++u) s[q] = csub_mul(s[q], x[u], Ps[(m + u - jb) * NB + q]);
             }
             for (; m < M; ++m) {
                 const float2 x = X[(long)m * M + i];
