@@ -29,6 +29,7 @@ namespace {
 
 constexpr int NB = 8;
 constexpr int SU = 8;          // rows of X loaded per step of the solves (loads in flight per thread)
+constexpr int TX = 3, TY = 3;  // complex micro-tile of the LU trailing update (fastest measured, 1x8 to 4x4)
 constexpr int PSTR = NB + 1;   // padded row stride of the LU panel (column reads conflict-free)
 constexpr int TILE = 32 * 33;  // one padded 32 x 32 transpose tile
 
@@ -255,42 +256,42 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
                 }
         }
         __syncthreads();
-        // A22 -= L21 U12 in 4 x 4 micro-tiles (rows and columns strided so
+        // A22 -= L21 U12 in TX x TY micro-tiles (rows and columns strided so
         // that a warp reads consecutive columns)
         const int nrr = M - c0;
         if (nrr > 0) {
-            const int tr = (nrr + 3) / 4, tc = (ncr + 3) / 4;
+            const int tr = (nrr + TX - 1) / TX, tc = (ncr + TY - 1) / TY;
             for (int t = tid; t < tr * tc; t += GT) {
                 const int rg = t / tc, cg = t % tc;
-                float2 acc[4][4];
+                float2 acc[TX][TY];
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < TX; ++x)
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) {
+                    for (int y = 0; y < TY; ++y) {
                         const int r = rg + x * tr, c = cg + y * tc;
                         acc[x][y] = (r < nrr && c < ncr) ? A[(long)(c0 + r) * M + c0 + c] : make_float2(0.f, 0.f);
                     }
                 for (int k = 0; k < nb; ++k) {
-                    float2 a[4], b[4];
+                    float2 a[TX], b[TY];
 #pragma unroll
-                    for (int x = 0; x < 4; ++x) {
+                    for (int x = 0; x < TX; ++x) {
                         const int r = rg + x * tr;
                         a[x] = r < nrr ? Ps[(nb + r) * PSTR + k] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) {
+                    for (int y = 0; y < TY; ++y) {
                         const int c = cg + y * tc;
                         b[y] = c < ncr ? Us[k * M + c] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < TX; ++x)
 #pragma unroll
-                        for (int y = 0; y < 4; ++y) acc[x][y] = csub_mul(acc[x][y], a[x], b[y]);
+                        for (int y = 0; y < TY; ++y) acc[x][y] = csub_mul(acc[x][y], a[x], b[y]);
                 }
 #pragma unroll
-                for (int x = 0; x < 4; ++x)
+                for (int x = 0; x < TX; ++x)
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) {
+                    for (int y = 0; y < TY; ++y) {
                         const int r = rg + x * tr, c = cg + y * tc;
                         if (r < nrr && c < ncr) A[(long)(c0 + r) * M + c0 + c] = acc[x][y];
                     }
