@@ -179,10 +179,9 @@ def set_device_peaks(torch, dev):
 # kernel as it stands (files under profiles/); the launches process walkers
 # independently with working sets far above L2, so traffic scales with the
 # walker count.  An entry is removed when its kernel changes.
-TRAFFIC_PER_WALKER = {
-    ("mixed", "green"): (1.054e9 / 128, "profiles/green32b_ueg_n66_m257_w128.md"),
-    ("mixed", "chain"): (0.3198e9 / 128, "profiles/chain_tc_ueg_n66_m257_w128.md"),
-    ("fp64", "chain"): (0.3867e9 / 128, "profiles/chain_fp64_ueg_n66_m257_w128.md"),
+TRAFFIC_PER_WALKER = {     # (bytes per walker, summary file, walkers in the capture)
+    ("mixed", "green"): ((15.486e9 + 5.508e9) / 608, "profiles/green32b_ueg_n66_m257_w608.md", 608),
+    ("fp64", "chain"): (0.3867e9 / 128, "profiles/chain_fp64_ueg_n66_m257_w128.md", 128),
 }
 
 
@@ -236,8 +235,8 @@ def roofline(prof, M, W, precision, green_tc=False):
            "traffic": None if tr is None else tr[0] * W, "peak_source": src, "avg_launch_ms": avg_s * 1e3,
            "share_of_step": share}
     if tr is not None:
-        out["traffic_source"] = (f"dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at 128 walkers "
-                                 f"({tr[1]}), scaled to {W} walkers")
+        out["traffic_source"] = (f"dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture at {tr[2]} "
+                                 f"walkers ({tr[1]}), scaled to {W} walkers")
     return out
 
 
