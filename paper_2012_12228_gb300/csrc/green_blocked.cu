@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
     __shared__ double shd[32];
     __shared__ double2 shc[32];
     __shared__ int nswap;
+    __shared__ double lsum_s;
+    __shared__ double2 ldm_s;
     __shared__ float2 rowp[NB], rowj[NB];
     const int tid = threadIdx.x;
     const int GT = blockDim.x;
@@ -128,7 +130,13 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
         lsum += log(b) + log(rb);
         perm[i] = i;
     }
-    if (tid == 0) nswap = 0;
+    // the two sums only thread 0 needs at the end are kept in shared memory,
+    // not in registers held through the LU and the solves
+    lsum = bsum(lsum, shd);
+    if (tid == 0) {
+        nswap = 0;
+        lsum_s = lsum;
+    }
     __syncthreads();
     {
         // 32 x 32 tiles: the chain planes are read along i (their contiguous
@@ -271,18 +279,16 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
                         const int r = rg + x * tr, c = cg + y * tc;
                         acc[x][y] = (r < nrr && c < ncr) ? A[(long)(c0 + r) * M + c0 + c] : make_float2(0.f, 0.f);
                     }
+                // unguarded shared reads: a row r < nrr + TX - 1 of the panel
+                // stays below row M + TX - 1 (the U12 region follows the
+                // panel), a column c < ncr + TY - 1 stays inside row k of U12;
+                // products of rows or columns past the edge are not stored
                 for (int k = 0; k < nb; ++k) {
                     float2 a[TX], b[TY];
 #pragma unroll
-                    for (int x = 0; x < TX; ++x) {
-                        const int r = rg + x * tr;
-                        a[x] = r < nrr ? Ps[(nb + r) * PSTR + k] : make_float2(0.f, 0.f);
-                    }
+                    for (int x = 0; x < TX; ++x) a[x] = Ps[(nb + rg + x * tr) * PSTR + k];
 #pragma unroll
-                    for (int y = 0; y < TY; ++y) {
-                        const int c = cg + y * tc;
-                        b[y] = c < ncr ? Us[k * M + c] : make_float2(0.f, 0.f);
-                    }
+                    for (int y = 0; y < TY; ++y) b[y] = Us[k * M + cg + y * tc];
 #pragma unroll
                     for (int x = 0; x < TX; ++x)
 #pragma unroll
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
         ldm = ldm + make_double2(0.5 * log(ux * ux + uy * uy), atan2(uy, ux));
     }
     ldm = bsum(ldm, shc);
-    lsum = bsum(lsum, shd);
+    if (tid == 0) ldm_s = ldm;
 
     // ---------------------------------------------------------------- X U = Y D_Rs
     for (int jb = 0; jb < M; jb += NB) {
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
     }
     trg = bsum(trg, shc);
     if (tid == 0)
-        green_weight_tail(ws + (long)WSTRIDE * w, ldm, lsum, nswap, trg, M, kdt, constraint, status);
+        green_weight_tail(ws + (long)WSTRIDE * w, ldm_s, lsum_s, nswap, trg, M, kdt, constraint, status);
 }
 
 }  // namespace
