@@ -239,29 +239,27 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
                 }
             }
         __syncthreads();
-        // U12 = L11^-1 A12, one column per thread
+        // U12 = L11^-1 A12, one column per thread.  Only a full panel has
+        // columns to its right (a narrower one is the last, nb = M - jb), so
+        // here and in the trailing update nb = NB.
         const int c0 = jb + nb;
         const int ncr = M - c0;
         for (int c = tid; c < ncr; c += GT) {
             float2 x[NB];
 #pragma unroll
-            for (int q = 0; q < NB; ++q)
-                if (q < nb) x[q] = A[(long)(jb + q) * M + c0 + c];
+            for (int q = 0; q < NB; ++q) x[q] = A[(long)(jb + q) * M + c0 + c];
 #pragma unroll
-            for (int q = 1; q < NB; ++q)
-                if (q < nb) {
-                    float2 s = x[q];
+            for (int q = 1; q < NB; ++q) {
+                float2 s = x[q];
 #pragma unroll
-                    for (int q2 = 0; q2 < NB; ++q2)
-                        if (q2 < q) s = csub_mul(s, Ps[q * PSTR + q2], x[q2]);
-                    x[q] = s;
-                }
+                for (int q2 = 0; q2 < q; ++q2) s = csub_mul(s, Ps[q * PSTR + q2], x[q2]);
+                x[q] = s;
+            }
 #pragma unroll
-            for (int q = 0; q < NB; ++q)
-                if (q < nb) {
-                    A[(long)(jb + q) * M + c0 + c] = x[q];
-                    Us[q * M + c] = x[q];
-                }
+            for (int q = 0; q < NB; ++q) {
+                A[(long)(jb + q) * M + c0 + c] = x[q];
+                Us[q * M + c] = x[q];
+            }
         }
         __syncthreads();
         // A22 -= L21 U12 in TX x TY micro-tiles (rows and columns strided so
@@ -283,10 +281,11 @@ __global__ void __launch_bounds__(GT_MAX, 4) k_green32b(const float* __restrict_
                 // stays below row M + TX - 1 (the U12 region follows the
                 // panel), a column c < ncr + TY - 1 stays inside row k of U12;
                 // products of rows or columns past the edge are not stored
-                for (int k = 0; k < nb; ++k) {
+#pragma unroll 1
+                for (int k = 0; k < NB; ++k) {
                     float2 a[TX], b[TY];
 #pragma unroll
-                    for (int x = 0; x < TX; ++x) a[x] = Ps[(nb + rg + x * tr) * PSTR + k];
+                    for (int x = 0; x < TX; ++x) a[x] = Ps[(NB + rg + x * tr) * PSTR + k];
 #pragma unroll
                     for (int y = 0; y < TY; ++y) b[y] = Us[k * M + cg + y * tc];
 #pragma unroll
