@@ -6,7 +6,7 @@
 //
 //   LU: NB-column panels factorised in shared memory; the row swaps are
 //       applied to the rest of the matrix column by column; U12 = L11^-1 A12
-//       one column per thread; A22 -= L21 U12 in 4 x 4 complex micro-tiles.
+//       one column per thread; A22 -= L21 U12 in 3 x 3 complex micro-tiles.
 //   X U = Y D_Rs and W L = X: NB-column blocks, one row per thread, the
 //       block of U (or L) staged in shared memory and broadcast; X is stored
 //       column-major so that a warp's loads of one column are contiguous.
@@ -16,7 +16,11 @@
 // the solves take one row per thread); matrices live in L2 / HBM.  The kernel
 // is latency-bound, so the panel width (NB = 8) and the register cap are
 // chosen for occupancy: four walkers per SM (a measured sweep over NB = 4, 8,
-// 16, 32 and one to five blocks per SM at M = 257).
+// 16, 32 and one to five blocks per SM at M = 257).  At that occupancy the
+// cap is 56 registers, and local-memory spills cost more than the shared
+// reads a larger micro-tile saves: values only thread 0 needs at the end are
+// parked in shared memory, and the hot loops carry no guards they can do
+// without.
 #include <cmath>
 
 #include "complex_math.cuh"
