@@ -180,6 +180,8 @@ def set_device_peaks(torch, dev):
 # independently with working sets far above L2, so traffic scales with the
 # walker count.  An entry is removed when its kernel changes.
 TRAFFIC_PER_WALKER = {     # (bytes per walker, summary file, walkers in the capture)
+    ("mixed", "green"): ((15.221e9 + 4.772e9) / 608, "profiles/green32b_ueg_n66_m257_w608.md", 608),
+    ("mixed", "chain"): ((0.43736e9 + 0.22356e9) / 256, "profiles/chain_tc_ueg_n66_m257_w256.md", 256),
     ("fp64", "chain"): (0.3867e9 / 128, "profiles/chain_fp64_ueg_n66_m257_w128.md", 128),
 }
 
